@@ -1,0 +1,187 @@
+"""Plain CPU oracle for the D1Q3 Monte Carlo Lattice Gas (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library under
+``paper_1706_01094_gb300`` never imports it, and this package never imports
+the library: the two share nothing but the seeded workload generators.
+
+``mclg_oracle.c`` holds the slow, plain reference (Philox4x32-10, the exact
+sub-collision sampler, streaming, Poisson initialisation, moments, exact
+statistics); this module builds it with gcc and wraps it with ctypes.
+``exact.py`` holds rational-arithmetic tools (enumeration of the paper's
+particle picks, stationary laws) used to pin it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mclg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERR_OVERFLOW = 1
+ERR_SAMPLER = 2
+FLAG_NO_STREAM = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+             "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            u32, u64, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+            lib.orc_philox.argtypes = [P, P, P]
+            lib.orc_feq.argtypes = [ctypes.c_double, ctypes.c_double, P]
+            lib.orc_poisson_inv.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_poisson_inv.restype = u32
+            lib.orc_init.argtypes = [P, u32, u64, P, P, P]
+            lib.orc_init.restype = i32
+            lib.orc_decide.argtypes = [u64, u64, u64, u32, P, i32, P]
+            lib.orc_decide.restype = i32
+            for name in ("orc_step", "orc_literal_step"):
+                fn = getattr(lib, name)
+                fn.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64]
+                fn.restype = i32
+            lib.orc_moments.argtypes = [P, u32, P, P, P, P]
+            lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
+            lib.orc_exact_cov.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, u64]
+            lib.orc_exact_cov.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _lengths(L) -> np.ndarray:
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
+    if L.size == 0 or (L == 0).any():
+        raise ValueError("every replica needs at least one node")
+    return L
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 4-word counter under a 2-word key."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def feq(rho: float, u: float) -> np.ndarray:
+    """Entropic D1Q3 equilibrium (f_-1, f_0, f_+1), Eq. D1Q3equil."""
+    f = np.zeros(3, dtype=np.float64)
+    _load().orc_feq(float(rho), float(u), _ptr(f))
+    return f
+
+
+def poisson_inv(mu: float, U: float) -> int:
+    return int(_load().orc_poisson_inv(float(mu), float(U)))
+
+
+def init(L, seed: int, rho, u) -> tuple[np.ndarray, int]:
+    """n_i(x, 0) ~ Poisson(f_i^eq(rho(x), u(x))); returns (n[3, S] uint16, error bits)."""
+    L = _lengths(L)
+    S = int(L.sum())
+    rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+    if rho.size != S or u.size != S:
+        raise ValueError("rho and u need one value per node")
+    n = np.zeros((3, S), dtype=np.uint16)
+    err = _load().orc_init(_ptr(L), L.size, seed & (2**64 - 1), _ptr(rho), _ptr(u), _ptr(n))
+    return n, int(err)
+
+
+def decide(T1: int, T2: int, D: int, q0: int, refine=()) -> tuple[int, int]:
+    """Region (0 down, 1 up, 2 nothing, -1 needs more chunks, -2 cap) and chunks used."""
+    ref = np.ascontiguousarray(np.asarray(list(refine), dtype=np.uint16))
+    if ref.size == 0:
+        ref = np.zeros(1, dtype=np.uint16)
+        nref = 0
+    else:
+        nref = ref.size
+    used = ctypes.c_int(0)
+    region = _load().orc_decide(T1, T2, D, q0, _ptr(ref), nref, ctypes.byref(used))
+    return int(region), int(used.value)
+
+
+def _run(fn_name, L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+    L = _lengths(L)
+    S = int(L.sum())
+    n = np.array(n, dtype=np.uint16, copy=True).reshape(3, S)
+    n = np.ascontiguousarray(n)
+    fn = getattr(_load(), fn_name)
+    err = fn(_ptr(L), L.size, seed & (2**64 - 1), C, lam[0], lam[1], flags, _ptr(n), t0, n_steps)
+    return n, int(err)
+
+
+def step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+    """Contract-mode time steps (bit-exact reference).  Returns (n, error bits)."""
+    return _run("orc_step", L, seed, n, t0, n_steps, C, lam, flags)
+
+
+def literal_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+    """The paper's particle-pick algorithm with its own random stream (distribution reference)."""
+    return _run("orc_literal_step", L, seed, n, t0, n_steps, C, lam, flags)
+
+
+def moments(L, n):
+    """Per-node N, J (int32) and exact int64 totals (sum N, sum J)."""
+    L = _lengths(L)
+    S = int(L.sum())
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.uint16).reshape(3, S))
+    N = np.zeros(S, dtype=np.int32)
+    J = np.zeros(S, dtype=np.int32)
+    tot = np.zeros(2, dtype=np.int64)
+    _load().orc_moments(_ptr(L), L.size, _ptr(n), _ptr(N), _ptr(J), _ptr(tot))
+    return N, J, tot
+
+
+class Stats:
+    """Exact int64 ensemble sums per node position, pooled over equal-length replicas."""
+
+    def __init__(self, Lc: int, R: int):
+        self.Lc, self.R = int(Lc), int(R)
+        self.s1 = np.zeros((self.Lc, 3), dtype=np.int64)
+        self.s2 = np.zeros((self.Lc, 6), dtype=np.int64)
+        self.snb = np.zeros((self.Lc, 9), dtype=np.int64)
+        self._count = np.zeros(1, dtype=np.uint64)
+
+    @property
+    def count(self) -> int:
+        return int(self._count[0])
+
+    def accumulate(self, n):
+        n = np.ascontiguousarray(np.asarray(n, dtype=np.uint16).reshape(3, self.Lc * self.R))
+        _load().orc_stats_accumulate(self.Lc, self.R, _ptr(n), _ptr(self.s1), _ptr(self.s2),
+                                     _ptr(self.snb), _ptr(self._count))
+
+    def cov(self, x: int, i: int, j: int) -> float:
+        """Exact covariance of n_i(x), n_j(x) from the int64 sums (FP64 only at the end)."""
+        pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+        p = pairs.index((min(i, j), max(i, j)))
+        return float(_load().orc_exact_cov(int(self.s2[x, p]), int(self.s1[x, i]),
+                                           int(self.s1[x, j]), self.count))

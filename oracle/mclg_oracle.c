@@ -1,0 +1,511 @@
+/*
+ * Plain CPU oracle for the D1Q3 Monte Carlo Lattice Gas (Blommel & Wagner,
+ * "Integer lattice gas with Monte Carlo collision operator recovers the
+ * entropic lattice Boltzmann method with Poisson distributed fluctuations").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library, its kernels or its Python
+ * binding may include, link or call this file; only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark use it.  It shares no code, header,
+ * table or constant generator with the CUDA path.
+ *
+ * Everything is written for clarity, not speed: nested loops over replicas,
+ * nodes and sub-collisions in the order the paper states them, 128-bit integer
+ * comparisons for the exact sampler, FP64 for the equilibrium and the Poisson
+ * initialisation.  Build with -ffp-contract=off (no fused multiply-add) so the
+ * FP64 initialisation is reproducible.
+ *
+ * State layout used by every function here: n[3 * S] uint16, S = sum of the
+ * replica lengths L[r]; plane i (0, 1, 2) holds the particles with velocity
+ * v = i - 1 (-1, 0, +1); replica r occupies nodes [off_r, off_r + L[r]) of
+ * each plane, off_r = L[0] + ... + L[r-1].  Lattices are periodic.
+ *
+ * Parity status of each function (pins live in tests/):
+ *   orc_philox        pinned: cuRAND host Philox4x32-10 (library call).
+ *   orc_feq           pinned: H-function minimiser (scipy), zero-velocity
+ *                     weights, Omega^(1) = 0 of Eq. collmatD1Q3.
+ *   orc_poisson_inv   pinned: scipy.stats.poisson.ppf.
+ *   orc_decide        pinned: exact enumeration of the chunk stream.
+ *   orc_step          pinned: exact rational enumeration of the paper's
+ *                     particle picks (Sec. III) for N <= 12; conservation and
+ *                     n_0 parity invariants; stationary law; Poisson means and
+ *                     variances against Eq. D1Q3equil and Eq. poisson.
+ *   orc_literal_step  pinned: same enumeration (its own random stream).
+ *   orc_init          pinned: sample mean/variance against Eq. D1Q3equil.
+ *   orc_moments       pinned: hand-computed small cases.
+ *   orc_stats_*       pinned: hand-computed small cases; numpy cross-check.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_ERR_OVERFLOW 1u /* a transition would leave [0, 65535] */
+#define ORC_ERR_SAMPLER 2u  /* decision still open after the refinement cap */
+
+#define ORC_FLAG_NO_STREAM 1u /* collide only: local equilibration (Sec. IV.A, Fig. decay) */
+
+/* Random-stream purposes (top 4 bits of the fourth Philox counter word). */
+#define PURPOSE_COLLIDE 0u
+#define PURPOSE_REFINE 1u
+#define PURPOSE_INIT 2u
+#define PURPOSE_LITERAL 3u
+
+#define CHUNKS_PER_BLOCK 10 /* 12-bit primary chunks per 128-bit Philox block */
+#define MAX_REFINE 4        /* 16-bit refinement chunks allowed per decision */
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two      */
+/* 32x32->64 multiplications; the key is advanced by the Weyl constants      */
+/* between rounds.                                                          */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void seed_key(uint64_t seed, uint32_t key[2])
+{
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+}
+
+/* The 128-bit value of one Philox block, word 0 least significant. */
+static unsigned __int128 block128(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                  const uint32_t key[2])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3}, w[4];
+    orc_philox(ctr, key, w);
+    unsigned __int128 b = 0;
+    for (int i = 3; i >= 0; i--) b = (b << 32) | w[i];
+    return b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entropic D1Q3 equilibrium, Eq. D1Q3equil:                                 */
+/*   f_i = rho w_i [1 + 3 v_i u + (3 v_i^2 - 1)(sqrt(1 + 3u^2) - 1)],         */
+/*   w_0 = 2/3, w_{+-1} = 1/6 (Eq. D1Q3wi).                                   */
+/* ------------------------------------------------------------------------ */
+void orc_feq(double rho, double u, double f[3])
+{
+    const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    double s = sqrt(1.0 + 3.0 * u * u) - 1.0;
+    for (int i = 0; i < 3; i++) {
+        double v = (double)(i - 1);
+        f[i] = rho * w[i] * (1.0 + 3.0 * v * u + (3.0 * v * v - 1.0) * s);
+    }
+}
+
+/* Poisson(mu) by inversion of the CDF: the smallest k with U < F(k), with the
+ * probabilities built by p_k = p_{k-1} * (mu / k) from p_0 = exp(-mu).  Used
+ * with mu <= 32 only; capped at k = 200. */
+uint32_t orc_poisson_inv(double mu, double U)
+{
+    double p = exp(-mu);
+    double F = p;
+    uint32_t k = 0;
+    while (U >= F && k < 200) {
+        k++;
+        p = p * (mu / (double)k);
+        F = F + p;
+    }
+    return k;
+}
+
+/* Initial occupations n_i ~ Poisson(f_i^eq(rho(x), u(x))) (Eq. poisson).
+ * Each mean is split into P = max(1, ceil(mu/32)) equal parts and the part
+ * samples are summed (a sum of independent Poisson variables is Poisson).
+ * Part p of plane i at (replica r, local node x) takes the uniform
+ *   U = ((w_hi << 32 | w_lo) >> 11) * 2^-53
+ * from Philox block (x, r, p/2, PURPOSE_INIT << 28 | i), words (0, 1) for
+ * even p and (2, 3) for odd p.  Returns ORC_ERR_OVERFLOW if a count exceeds
+ * 65535, 8 for an invalid (rho, u) (negative, non-finite or |u| > 1). */
+int orc_init(const uint32_t *L, uint32_t R, uint64_t seed, const double *rho, const double *u,
+             uint16_t *n)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < R; r++) S += L[r];
+    int err = 0;
+    uint64_t off = 0;
+    for (uint32_t r = 0; r < R; r++) {
+        for (uint32_t x = 0; x < L[r]; x++) {
+            double rh = rho[off + x], uu = u[off + x];
+            if (!(rh >= 0.0) || !isfinite(rh) || !(fabs(uu) <= 1.0)) return 8;
+            double f[3];
+            orc_feq(rh, uu, f);
+            for (uint32_t i = 0; i < 3; i++) {
+                double mu = f[i] > 0.0 ? f[i] : 0.0;
+                uint32_t parts = (uint32_t)ceil(mu / 32.0);
+                if (parts < 1) parts = 1;
+                double mup = mu / (double)parts;
+                uint64_t total = 0;
+                for (uint32_t p = 0; p < parts; p++) {
+                    uint32_t ctr[4] = {x, r, p / 2, (PURPOSE_INIT << 28) | i}, w[4];
+                    orc_philox(ctr, key, w);
+                    uint32_t lo = (p % 2 == 0) ? w[0] : w[2];
+                    uint32_t hi = (p % 2 == 0) ? w[1] : w[3];
+                    uint64_t m = (((uint64_t)hi << 32) | lo) >> 11;
+                    double U = (double)m * (1.0 / 9007199254740992.0);
+                    total += orc_poisson_inv(mup, U);
+                }
+                if (total > 65535) {
+                    err |= ORC_ERR_OVERFLOW;
+                    total = 65535;
+                }
+                n[i * S + off + x] = (uint16_t)total;
+            }
+        }
+        off += L[r];
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact sampler of one sub-collision.                                       */
+/*                                                                          */
+/* With particles picked by two independent uniform draws of a particle      */
+/* index in [1, N] (Eq. select; picking the same particle twice collides     */
+/* nothing) and the D1Q3 table of Sec. III.A:                                */
+/*   P(down: (a,b,c) -> (a-1,b+2,c-1)) = 2ac/N^2 * lambda        = T1/D      */
+/*   P(up:   (a,b,c) -> (a+1,b-2,c+1)) = b(b-1)/N^2 * lambda/8   = (T2-T1)/D */
+/* with T1 = 16 a c lam_n, T2 = T1 + b (b-1) lam_n, D = 8 N^2 lam_d,          */
+/* (a, b, c) = (n_-1, n_0, n_+1), lambda = lam_n / lam_d.                    */
+/*                                                                          */
+/* The outcome is the region of a uniform real U in [0,1) against T1/D and  */
+/* T2/D: U < T1/D -> down, T1/D <= U < T2/D -> up, otherwise nothing.  U's   */
+/* binary expansion is a 12-bit primary chunk q0 followed, only while the    */
+/* region is still open, by 16-bit refinement chunks.  Knowing the first     */
+/* `bits` bits Q places U in [Q, Q+1) / 2^bits, so U < T/D is certain when    */
+/* (Q+1) D <= T 2^bits and U >= T/D is certain when Q D >= T 2^bits.          */
+/*                                                                          */
+/* Returns 0 (down), 1 (up), 2 (nothing), -1 when more refinement chunks are */
+/* needed than `nref` supplies, -2 past the MAX_REFINE cap.  *used = number  */
+/* of refinement chunks read.                                               */
+/* ------------------------------------------------------------------------ */
+typedef int (*chunk_source)(void *ctx, int k, uint16_t *chunk); /* 0 = no chunk k */
+
+static int decide(uint64_t T1, uint64_t T2, uint64_t D, uint32_t q0, chunk_source src, void *ctx,
+                  int *used)
+{
+    unsigned __int128 Q = q0;
+    int bits = 12;
+    *used = 0;
+    for (int k = 0;; k++) {
+        unsigned __int128 lo = Q * (unsigned __int128)D;
+        unsigned __int128 hi = lo + D;
+        unsigned __int128 s1 = (unsigned __int128)T1 << bits;
+        unsigned __int128 s2 = (unsigned __int128)T2 << bits;
+        if (hi <= s1) return 0;
+        if (lo >= s1 && hi <= s2) return 1;
+        if (lo >= s2) return 2;
+        if (k == MAX_REFINE) return -2;
+        uint16_t next;
+        if (!src(ctx, k, &next)) return -1;
+        Q = (Q << 16) | next;
+        bits += 16;
+        *used = k + 1;
+    }
+}
+
+typedef struct {
+    const uint16_t *chunks;
+    int n;
+} chunk_array;
+
+static int from_array(void *ctx, int k, uint16_t *chunk)
+{
+    chunk_array *a = (chunk_array *)ctx;
+    if (k >= a->n) return 0;
+    *chunk = a->chunks[k];
+    return 1;
+}
+
+int orc_decide(uint64_t T1, uint64_t T2, uint64_t D, uint32_t q0, const uint16_t *ref, int nref,
+               int *used)
+{
+    chunk_array a = {ref, nref};
+    return decide(T1, T2, D, q0, from_array, &a, used);
+}
+
+/* Refinement chunk s of the node-step (x, r, t): 16-bit chunk s % 8 of Philox
+ * block (x, r, t, PURPOSE_REFINE << 28 | s / 8), chunk m = bits [16m, 16m+16). */
+static uint16_t refine_chunk(uint32_t x, uint32_t r, uint32_t t, uint32_t s, const uint32_t key[2])
+{
+    unsigned __int128 b = block128(x, r, t, (PURPOSE_REFINE << 28) | (s / 8), key);
+    return (uint16_t)((b >> (16 * (s % 8))) & 0xFFFF);
+}
+
+typedef struct {
+    uint32_t x, r, t, first;
+    const uint32_t *key;
+} refine_stream;
+
+static int from_refine_stream(void *ctx, int k, uint16_t *chunk)
+{
+    refine_stream *rs = (refine_stream *)ctx;
+    *chunk = refine_chunk(rs->x, rs->r, rs->t, rs->first + (uint32_t)k, rs->key);
+    return 1;
+}
+
+/* Primary chunk of sub-collision c of the node-step (x, r, t): 12-bit chunk
+ * m = c % 10 (bits [12m, 12m+12)) of Philox block (x, r, t, c / 10). */
+static uint32_t primary_chunk(uint32_t x, uint32_t r, uint32_t t, uint32_t c, const uint32_t key[2])
+{
+    unsigned __int128 b = block128(x, r, t, (PURPOSE_COLLIDE << 28) | (c / CHUNKS_PER_BLOCK), key);
+    return (uint32_t)((b >> (12 * (c % CHUNKS_PER_BLOCK))) & 0xFFF);
+}
+
+/* C sequential sub-collisions at one node (Sec. III, Eqs. select and omega):
+ * each sub-collision acts on the state left by the previous one.  A node with
+ * N < 2 has no pair to collide and is left as it is. */
+static int collide_node(uint16_t st[3], uint32_t x, uint32_t r, uint32_t t, uint32_t C,
+                        uint32_t lam_n, uint32_t lam_d, const uint32_t key[2])
+{
+    uint64_t a = st[0], b = st[1], c = st[2];
+    uint64_t N = a + b + c;
+    if (N < 2) return 0;
+    uint64_t D = 8 * N * N * lam_d;
+    uint32_t next_ref = 0; /* refinement chunks are consumed in order across the node-step */
+    for (uint32_t k = 0; k < C; k++) {
+        uint64_t T1 = 16 * a * c * lam_n;
+        uint64_t T2 = T1 + (b > 0 ? b * (b - 1) : 0) * lam_n;
+        uint32_t q0 = primary_chunk(x, r, t, k, key);
+        refine_stream rs = {x, r, t, next_ref, key};
+        int used = 0;
+        int region = decide(T1, T2, D, q0, from_refine_stream, &rs, &used);
+        next_ref += (uint32_t)used;
+        if (region == -2) {
+            st[0] = (uint16_t)a; st[1] = (uint16_t)b; st[2] = (uint16_t)c;
+            return ORC_ERR_SAMPLER;
+        }
+        if (region == 0) { /* {-1, 1} -> {0, 0} */
+            if (b + 2 > 65535) {
+                st[0] = (uint16_t)a; st[1] = (uint16_t)b; st[2] = (uint16_t)c;
+                return ORC_ERR_OVERFLOW;
+            }
+            a -= 1; b += 2; c -= 1;
+        } else if (region == 1) { /* {0, 0} -> {-1, 1} */
+            if (a + 1 > 65535 || c + 1 > 65535) {
+                st[0] = (uint16_t)a; st[1] = (uint16_t)b; st[2] = (uint16_t)c;
+                return ORC_ERR_OVERFLOW;
+            }
+            a += 1; b -= 2; c += 1;
+        }
+    }
+    st[0] = (uint16_t)a; st[1] = (uint16_t)b; st[2] = (uint16_t)c;
+    return 0;
+}
+
+/* Streaming, from the evolution equation n_i(x + v_i, t + 1) = n_i(x, t) + Xi_i
+ * (Sec. III): post-collision particles at x move to x + v_i, periodically. */
+static void stream(const uint32_t *L, uint32_t R, uint64_t S, const uint16_t *post, uint16_t *n)
+{
+    uint64_t off = 0;
+    for (uint32_t r = 0; r < R; r++) {
+        uint32_t Lr = L[r];
+        for (uint32_t x = 0; x < Lr; x++) {
+            for (int i = 0; i < 3; i++) {
+                int v = i - 1;
+                uint32_t dest = (uint32_t)(((int64_t)x + v + Lr) % Lr);
+                n[i * S + off + dest] = post[i * S + off + x];
+            }
+        }
+        off += Lr;
+    }
+}
+
+/* n_steps time steps from time t0.  n holds the pre-collision occupations
+ * n_i(x, t0) on entry and n_i(x, t0 + n_steps) on return.  Collision at
+ * (replica r, local node x, time t) draws from Philox counters (x, r, t, .)
+ * with key (seed low 32 bits, seed high 32 bits).  Returns ORC_ERR_* bits;
+ * after an error the state is unspecified. */
+int orc_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
+             uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < R; r++) S += L[r];
+    uint16_t *post = (uint16_t *)malloc(3 * S * sizeof(uint16_t) + 1);
+    if (!post) return 16;
+    int err = 0;
+    for (uint64_t s = 0; s < n_steps; s++) {
+        uint32_t t = (uint32_t)(t0 + s);
+        uint64_t off = 0;
+        for (uint32_t r = 0; r < R; r++) {
+            for (uint32_t x = 0; x < L[r]; x++) {
+                uint16_t st[3] = {n[0 * S + off + x], n[1 * S + off + x], n[2 * S + off + x]};
+                err |= collide_node(st, x, r, t, C, lam_n, lam_d, key);
+                for (int i = 0; i < 3; i++) post[i * S + off + x] = st[i];
+            }
+            off += L[r];
+        }
+        if (flags & ORC_FLAG_NO_STREAM)
+            memcpy(n, post, 3 * S * sizeof(uint16_t));
+        else
+            stream(L, R, S, post, n);
+    }
+    free(post);
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Literal form of the paper's algorithm (Sec. III): two uniform particle    */
+/* indices r1, r2 in [1, N]; r -> velocity by cumulative counts in the order */
+/* (-1, 0, +1) (Eq. select); the same particle twice collides nothing; then  */
+/* the D1Q3 table of Sec. III.A.  Its random numbers come from a stream of   */
+/* its own (PURPOSE_LITERAL), so it is a distribution reference, not a       */
+/* bit-exact one.                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint32_t x, r, t, blk, pos;
+    uint32_t w[4];
+    const uint32_t *key;
+} word_stream;
+
+static uint32_t next_word(word_stream *ws)
+{
+    if (ws->pos == 4) {
+        uint32_t ctr[4] = {ws->x, ws->r, ws->t, (PURPOSE_LITERAL << 28) | ws->blk};
+        orc_philox(ctr, ws->key, ws->w);
+        ws->blk++;
+        ws->pos = 0;
+    }
+    return ws->w[ws->pos++];
+}
+
+/* Uniform integer in [0, m) by rejection of the incomplete top range. */
+static uint32_t uniform_below(word_stream *ws, uint32_t m)
+{
+    uint32_t limit = (uint32_t)((((uint64_t)1 << 32) / m) * m - 1);
+    for (;;) {
+        uint32_t w = next_word(ws);
+        if (w <= limit) return w % m;
+    }
+}
+
+int orc_literal_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
+                     uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < R; r++) S += L[r];
+    uint16_t *post = (uint16_t *)malloc(3 * S * sizeof(uint16_t) + 1);
+    if (!post) return 16;
+    int err = 0;
+    for (uint64_t s = 0; s < n_steps; s++) {
+        uint32_t t = (uint32_t)(t0 + s);
+        uint64_t off = 0;
+        for (uint32_t r = 0; r < R; r++) {
+            for (uint32_t x = 0; x < L[r]; x++) {
+                int64_t cnt[3] = {n[off + x], n[S + off + x], n[2 * S + off + x]};
+                word_stream ws = {x, r, t, 0, 4, {0, 0, 0, 0}, key};
+                uint32_t N = (uint32_t)(cnt[0] + cnt[1] + cnt[2]);
+                for (uint32_t k = 0; k < C && N >= 2; k++) {
+                    uint32_t r1 = 1 + uniform_below(&ws, N);
+                    uint32_t r2 = 1 + uniform_below(&ws, N);
+                    int s1 = r1 <= cnt[0] ? 0 : (r1 <= cnt[0] + cnt[1] ? 1 : 2);
+                    int s2 = r2 <= cnt[0] ? 0 : (r2 <= cnt[0] + cnt[1] ? 1 : 2);
+                    if (r1 == r2) continue; /* one particle cannot collide with itself */
+                    if ((s1 == 0 && s2 == 2) || (s1 == 2 && s2 == 0)) {
+                        /* P_{-1 1 -> 0 0} = P_{1 -1 -> 0 0} = lambda */
+                        if (uniform_below(&ws, lam_d) < lam_n) {
+                            cnt[0] -= 1; cnt[1] += 2; cnt[2] -= 1;
+                        }
+                    } else if (s1 == 1 && s2 == 1) {
+                        /* P_{00 -> -1 1} = P_{00 -> 1 -1} = lambda / 16 */
+                        uint32_t v = uniform_below(&ws, 16 * lam_d);
+                        if (v < 2 * lam_n) {
+                            cnt[0] += 1; cnt[1] -= 2; cnt[2] += 1;
+                        }
+                    }
+                }
+                for (int i = 0; i < 3; i++) {
+                    if (cnt[i] < 0 || cnt[i] > 65535) err |= ORC_ERR_OVERFLOW;
+                    post[i * S + off + x] = (uint16_t)cnt[i];
+                }
+            }
+            off += L[r];
+        }
+        if (flags & ORC_FLAG_NO_STREAM)
+            memcpy(n, post, 3 * S * sizeof(uint16_t));
+        else
+            stream(L, R, S, post, n);
+    }
+    free(post);
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Node moments: mass N = sum_i n_i (Sec. III) and momentum J = N U =         */
+/* sum_i n_i v_i = n_+1 - n_-1 (Sec. IV.A); exact int64 totals.              */
+/* ------------------------------------------------------------------------ */
+void orc_moments(const uint32_t *L, uint32_t R, const uint16_t *n, int32_t *N, int32_t *J,
+                 int64_t totals[2])
+{
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < R; r++) S += L[r];
+    totals[0] = 0;
+    totals[1] = 0;
+    for (uint64_t x = 0; x < S; x++) {
+        int32_t a = n[x], b = n[S + x], c = n[2 * S + x];
+        N[x] = a + b + c;
+        J[x] = c - a;
+        totals[0] += N[x];
+        totals[1] += J[x];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ensemble statistics for Eqs. poisson, Poisson2, corr and error: per node  */
+/* position x (all replicas have the same length L and are pooled),          */
+/*   s1[3*x + i]       += n_i(x)                                             */
+/*   s2[6*x + p]       += n_i(x) n_j(x),     p over (i,j) = 00 01 02 11 12 22 */
+/*   snb[9*x + 3*i+j]  += n_i(x) n_j(x+1 mod L)                              */
+/* and the sample count.  Exact in int64.                                   */
+/* ------------------------------------------------------------------------ */
+void orc_stats_accumulate(uint32_t Lc, uint32_t R, const uint16_t *n, int64_t *s1, int64_t *s2,
+                          int64_t *snb, uint64_t *count)
+{
+    static const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    uint64_t S = (uint64_t)Lc * R;
+    for (uint32_t r = 0; r < R; r++) {
+        for (uint32_t x = 0; x < Lc; x++) {
+            uint64_t g = (uint64_t)r * Lc + x;
+            uint64_t g1 = (uint64_t)r * Lc + (x + 1) % Lc;
+            int64_t v[3] = {n[g], n[S + g], n[2 * S + g]};
+            int64_t w[3] = {n[g1], n[S + g1], n[2 * S + g1]};
+            for (int i = 0; i < 3; i++) s1[3 * (uint64_t)x + i] += v[i];
+            for (int p = 0; p < 6; p++) s2[6 * (uint64_t)x + p] += v[pi[p]] * v[pj[p]];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) snb[9 * (uint64_t)x + 3 * i + j] += v[i] * w[j];
+        }
+    }
+    *count += R;
+}
+
+/* Exact (co)variance from the int64 sums: (M s_ij - s_i s_j) / M^2, the
+ * numerator in 128-bit integers, one FP64 division at the end. */
+double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
+{
+    __int128 num = (__int128)M * sij - (__int128)si * sj;
+    long double d = (long double)M * (long double)M;
+    return (double)((long double)num / d);
+}
