@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the D1Q3 Monte Carlo Lattice Gas step on GB300.
+
+One "step" is one MCLG time step (pull streaming + C = 10 exact random
+sub-collisions per node) of the whole workload.  Default workload: one
+periodic lattice of 2^24 nodes, rho = 100 (1 + 0.01 sin(2 pi 4 x / L)), u = 0,
+Poisson(f^eq) initial state (the paper-shaped single-lattice run), 10^4 steps
+timed after the warm-up.  The state (192 MiB double-buffered) is larger than
+L2, so no flush is needed between steps.
+
+Metric: GSUPS = node updates per second / 1e9, whole job (all ranks).
+Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1706_01094_gb300 import workloads  # noqa: E402
+
+METRIC = "MCLG site updates/sec (GSUPS), D1Q3 C=10 lambda=1, bit-exact vs CPU oracle"
+BYTES_PER_NODE_STEP = 12        # 3 uint16 read + 3 uint16 written
+# Algorithmic integer operations per node-step at C <= 10 (one Philox block):
+# Philox4x32-10 = 10 rounds x (2 mul-hi + 2 mul-lo + 4 xor) + 9 x 2 key adds = 98;
+# each sub-collision = 3 mul (a c, b (b-1), q D) + 2 shifts + 1 add (thresholds)
+# + 4 compares + 3 adds (state update) = 13, times C = 10.
+INT_OPS_PER_NODE_STEP = 98 + 13 * 10
+INT32_LANES_PER_SM_CLK = 64     # integer pipe lanes per SM and clock
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10_000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "uneven"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def committed_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str):
+    return workloads.BY_NAME[name]()
+
+
+def sample_workload(wl, nodes: int):
+    """A bounded sample of the workload: its first replicas (whole) up to about
+    `nodes` nodes, or for a single lattice a periodic window of `nodes` nodes
+    with the same density and velocity profile values."""
+    from dataclasses import replace
+    if wl.replicas == 1:
+        m = max(8, min(int(nodes), wl.nodes))
+        return replace(wl, L=np.array([m], dtype=np.uint32), rho=wl.rho[:m], u=wl.u[:m])
+    cum = np.cumsum(wl.L.astype(np.int64))
+    k = int(max(1, np.searchsorted(cum, nodes, side="right")))
+    m = int(cum[k - 1])
+    return replace(wl, L=wl.L[:k].copy(), rho=wl.rho[:m], u=wl.u[:m])
+
+
+def oracle_rate(wl, seconds: float):
+    """Time the CPU oracle (single thread, as it stands) for about `seconds` on a
+    bounded sample of the workload; returns (GSUPS, sample description)."""
+    import oracle
+    oracle.build()
+    probe = sample_workload(wl, 1 << 16)
+    n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
+    t0 = time.perf_counter()
+    n, err = oracle.step(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
+    rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
+    sw = sample_workload(wl, min(wl.nodes, max(1 << 12, int(rate * seconds / 4))))
+    steps = max(1, int(rate * seconds / sw.nodes))
+    n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
+    assert err == 0
+    t0 = time.perf_counter()
+    n, err = oracle.step(sw.L, sw.seed, n, 0, steps, C=sw.C, lam=sw.lam)
+    dt = time.perf_counter() - t0
+    sample = (f"{steps} time step(s) of a {sw.nodes}-node, {sw.replicas}-replica sample of the "
+              f"workload (same profile values), {dt:.1f} s")
+    return sw.nodes * steps / dt / 1e9, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    # size the per-step sample so that warm-up + timed steps take about two minutes
+    probe = sample_workload(wl, 1 << 16)
+    n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
+    t0 = time.perf_counter()
+    oracle.step(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
+    rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    sw = sample_workload(wl, max(1024, int(rate * per_step)))
+    n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
+    assert err == 0
+    t = 0
+    for _ in range(args.warmup):
+        n, err = oracle.step(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
+        t += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        n, err = oracle.step(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
+        t += 1
+    dt = time.perf_counter() - t0
+    value = sw.nodes * args.steps / dt / 1e9
+    sample = (f"each step: one time step of a {sw.nodes}-node, {sw.replicas}-replica sample of "
+              f"the workload (same profile values)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GSUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": config_dict(wl, args, world),
+            "cpu_baseline": {"value": value, "unit": "GSUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GSUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(wl, args, world):
+    return {"workload": f"{wl.name}: {wl.replicas} replica(s), {wl.nodes} nodes, C={wl.C}, "
+                        f"lambda={wl.lam[0]}/{wl.lam[1]}",
+            "replicas_per_gpu": wl.replicas, "nodes_per_gpu": wl.nodes,
+            "global_nodes": wl.nodes * world, "C": wl.C, "seed": wl.seed,
+            "parallelism": f"independent lattices x{world}",
+            "l2": "state (12 B/node double-buffered) larger than L2; no flush" if wl.nodes * 12 > 129e6
+                  else "state L2-resident"}
+
+
+def run_gb300(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1706_01094_gb300 import build, mclg
+    build.build()
+    wl = make_workload(args.workload)
+    mode = {"auto": mclg.MODE_AUTO, "plain": mclg.MODE_PLAIN, "persistent": mclg.MODE_PERSISTENT,
+            "batched": mclg.MODE_BATCHED}[args.mode]
+    stream = torch.cuda.Stream()
+    seed = wl.seed + rank  # each rank runs its own independent lattice(s)
+    lat = mclg.Lattice(wl.L, seed=seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream)
+    lat.init(wl.rho, wl.u)
+    tot0 = lat.totals()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also runs the persistent autotuner when it applies)
+    lat.step(args.warmup)
+    lat.sync()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        if mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1):
+            lat.step(args.steps)
+            launches = None
+        else:
+            for _ in range(args.steps):
+                lat.step(1)
+            launches = args.steps * (wl.replicas if mode == mclg.MODE_PLAIN else 1)
+        ev1.record(stream)
+        ev1.synchronize()
+    lat.sync()
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    # correctness guard on the timed run: exact conservation of mass and momentum
+    assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
+    node_steps = wl.nodes * args.steps
+    value = node_steps * world / (t_max / 1e3) / 1e9
+    if launches is None:
+        n_units = None
+        launches = 1 + (0 if wl.replicas == 1 else 0)
+
+    # end to end through the C ABI with pinned host buffers: every step uploads
+    # the state, advances one step and reads the new state back
+    host_in = torch.empty((3, wl.nodes), dtype=torch.int16).pin_memory()
+    host_out = torch.empty((3, wl.nodes), dtype=torch.int16).pin_memory()
+    st, _ = lat.get_state()
+    host_in.copy_(torch.from_numpy(st.view(np.int16)))
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tcur = lat.t
+    for k in range(e2e_steps):
+        lat.set_state(host_in, t=tcur + k)
+        lat.step(1)
+        lat.get_state(host_out)
+    e2e_dt = time.perf_counter() - t0
+    e2e_dt_max = e2e_dt
+    if world > 1:
+        tt = torch.tensor([e2e_dt], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_dt_max = float(tt.item())
+    e2e_value = wl.nodes * e2e_steps * world / e2e_dt_max / 1e9
+    lat.close()
+
+    if rank == 0:
+        pk = peaks()
+        hbm_peak = pk.get("hbm_gbs", 6800.0)
+        sm_max = pk.get("sm_max_mhz", 2070.0)
+        clk = clocks.summary()
+        ms_launch = ms / max(1, launches) if launches else ms
+        per_launch_nodes = wl.nodes if args.mode != "plain" or wl.replicas == 1 else None
+        alu_peak = INT32_LANES_PER_SM_CLK * SMS * sm_max * 1e6 / 1e9  # Gop/s
+        achieved_ops = INT_OPS_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
+        achieved_gbs = BYTES_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
+        kernel = "k_step_plain" if (wl.replicas == 1 or args.mode in ("plain", "batched")) else "k_step_persistent"
+        traffic = committed_traffic(kernel, wl.name)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GSUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic: Poisson(f^eq) initial state of the paper-shaped workload",
+            "config": config_dict(wl, args, world),
+            "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
+                         "unit": "Gop/s", "frac": achieved_ops / alu_peak,
+                         "traffic": traffic, "kernel": kernel,
+                         "ops_per_node_step": INT_OPS_PER_NODE_STEP,
+                         "peak_basis": f"{INT32_LANES_PER_SM_CLK} int32 lanes x {SMS} SMs x {sm_max:.0f} MHz",
+                         "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": achieved_gbs / hbm_peak,
+                                 "bytes_per_node_step": BYTES_PER_NODE_STEP,
+                                 "peak_basis": "measured copy bandwidth"}},
+            "e2e": {"value": e2e_value, "unit": "GSUPS",
+                    "h2d_bytes_per_step": 6 * wl.nodes, "d2h_bytes_per_step": 6 * wl.nodes,
+                    "steps": e2e_steps,
+                    "path": "mclg_set_state(pinned host) + mclg_step(1) + mclg_get_state(pinned host)"},
+            "gpu_launches": launches,
+            "ms_per_launch": ms_launch,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, sample = oracle_rate(wl, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": "GSUPS", "cores": 1, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

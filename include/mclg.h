@@ -1,0 +1,155 @@
+/*
+ * mclg.h - C ABI of the GB300 (sm_103a) D1Q3 Monte Carlo Lattice Gas library.
+ *
+ * The method (Blommel & Wagner, arXiv:1706.01094): integer occupation numbers
+ * n_i(x, t), i <-> v_i in {-1, 0, +1}, on periodic 1D lattices evolve by
+ *     n_i(x + v_i, t + 1) = n_i(x, t) + Xi_i                      (Sec. III)
+ * where Xi is the sum of C random binary sub-collisions at each node, each
+ * acting on the state left by the previous one.  A sub-collision picks two
+ * particles uniformly (Eq. select) and applies the D1Q3 table of Sec. III.A:
+ * {-1, +1} -> {0, 0} with probability lambda, {0, 0} -> {-1, +1} with
+ * probability lambda/8 (two orderings of lambda/16).  Mass N = sum n_i and
+ * momentum J = n_+1 - n_-1 are conserved exactly at every node.
+ *
+ * Exact sampling contract (identical on every execution path, so results do
+ * not depend on the kernel, tile shape or batch composition):
+ *   - Random bits: Philox4x32-10, key (seed & 0xffffffff, seed >> 32),
+ *     counter (x, r, t, purpose << 28 | block) with x the replica-local node,
+ *     r the replica index, t the time step (t < 2^32).
+ *   - Sub-collision k at node (x, r) and time t draws a uniform real U whose
+ *     first 12 bits are bits [12m, 12m+12) (m = k % 10) of the 128-bit block
+ *     (x, r, t, k / 10) (word 0 least significant); while U's region is still
+ *     undecided, the next bits come as 16-bit chunks, in order, from blocks
+ *     (x, r, t, 1 << 28 | j) (chunk s = bits [16(s%8), 16(s%8)+16) of block
+ *     j = s / 8), counted across the node's whole time step.
+ *   - With (a, b, c) = (n_-1, n_0, n_+1), N = a + b + c, lambda = ln / ld:
+ *     T1 = 16 a c ln, T2 = T1 + b (b - 1) ln, D = 8 N^2 ld.
+ *     U < T1/D: (a-1, b+2, c-1); T1/D <= U < T2/D: (a+1, b-2, c+1); else no
+ *     change.  Nodes with N < 2 are left as they are.
+ *   - Initial occupations (mclg_init): n_i ~ Poisson(f_i^eq(rho, u)) with the
+ *     entropic equilibrium of Eq. D1Q3equil, sampled on the host in FP64 by
+ *     CDF inversion over parts of mean <= 32 (purpose 2).
+ *
+ * Layout of every state array crossing this ABI: uint16 n[3][S], S = sum of
+ * the replica lengths, plane i = 0, 1, 2 for v = -1, 0, +1, replica r at
+ * nodes [L[0] + ... + L[r-1], ... + L[r]).  Arrays may be host or device
+ * pointers (detected with cudaPointerGetAttributes).
+ *
+ * Ownership: the library owns every device buffer it allocates; the caller
+ * owns every array it passes and may free it when the call returns.
+ * Errors: every call returns an mclg_status; nothing is thrown across the
+ * ABI.  Device-side errors (overflow, sampler cap) are sticky: they are
+ * reported by mclg_sync and by every later call until mclg_init or
+ * mclg_set_state replaces the state.  A handle is not thread-safe; all its
+ * work is ordered on its CUDA stream.
+ */
+#ifndef MCLG_H
+#define MCLG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mclg_ctx *mclg_handle;
+
+typedef enum {
+    MCLG_OK = 0,
+    MCLG_ERR_ARG = 1,      /* invalid argument */
+    MCLG_ERR_NOMEM = 2,    /* device or host allocation failed */
+    MCLG_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    MCLG_ERR_OVERFLOW = 4, /* an occupation would leave [0, 65535]; state unspecified */
+    MCLG_ERR_TIMEOUT = 5,  /* reserved: a bounded device-side wait gave up */
+    MCLG_ERR_STATE = 6,    /* no state yet (call mclg_init or mclg_set_state) */
+    MCLG_ERR_SAMPLER = 7   /* a decision stayed open after 4 refinement chunks (p < 2^-70) */
+} mclg_status;
+
+/* flags */
+#define MCLG_NO_STREAM 1u /* collide only, no streaming (the "without streaming" runs of Fig. decay) */
+#define MCLG_STATS 2u     /* accumulate ensemble statistics after every step (Sec. V) */
+
+/* execution modes; every mode gives bit-identical results */
+#define MCLG_MODE_AUTO 0u       /* persistent batch where it pays, plain otherwise */
+#define MCLG_MODE_PLAIN 1u      /* one plain-kernel launch per replica and step */
+#define MCLG_MODE_PERSISTENT 2u /* replicas resident on chip for many steps, one launch */
+
+typedef struct {
+    uint32_t C;          /* sub-collisions per node and step (paper: C = 10, Sec. III.A, IV.A) */
+    uint32_t lambda_num; /* lambda = lambda_num / lambda_den, 0 <= lambda <= 1 (Sec. III.A) */
+    uint32_t lambda_den; /* 1 <= lambda_den <= 256 */
+    uint32_t flags;      /* MCLG_NO_STREAM | MCLG_STATS */
+    uint32_t mode;       /* MCLG_MODE_* */
+} mclg_params;
+
+/* Defaults: C = 10, lambda = 1, flags 0, mode AUTO (the paper's D1Q3 runs). */
+void mclg_default_params(mclg_params *p);
+
+/* Create a handle for `replicas` independent periodic lattices of lengths
+ * L[0..replicas-1] (1 <= L[r] <= 2^31, sum L < 2^40), Philox seed `seed`.
+ * p = NULL selects the defaults; cuda_stream = NULL uses the legacy default
+ * stream.  Allocates the device state; no state is set yet.
+ * MCLG_STATS requires all replicas to have the same length. */
+mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, const mclg_params *p,
+                        void *cuda_stream, mclg_handle *out);
+
+/* n_i(x, 0) ~ Poisson(f_i^eq(rho(x), u(x))) with f^eq of Eq. D1Q3equil; rho, u
+ * are host arrays of S doubles (rho >= 0, |u| <= 1).  Sets t = 0 and clears the
+ * sticky error.  MCLG_ERR_OVERFLOW if a sampled count exceeds 65535. */
+mclg_status mclg_init(mclg_handle h, const double *rho, const double *u);
+
+/* Replace the state by the pre-collision field n(x, t) (layout above, host or
+ * device pointer) at time t (t < 2^32).  Clears the sticky error. */
+mclg_status mclg_set_state(mclg_handle h, const uint16_t *n, uint64_t t);
+
+/* Copy the pre-collision field n(x, t) of the current time t into n (host or
+ * device) and t into *t (may be NULL).  Synchronises the handle's stream. */
+mclg_status mclg_get_state(mclg_handle h, uint16_t *n, uint64_t *t);
+
+/* Advance n_steps time steps (stream + C sub-collisions per node, Sec. III).
+ * Asynchronous: returns once the work is enqueued.  Returns the sticky error
+ * of earlier work if one is known. */
+mclg_status mclg_step(mclg_handle h, uint64_t n_steps);
+
+/* Node moments of the current state: N(x) = sum_i n_i and J(x) = n_+1 - n_-1
+ * (int32, S entries each, host or device, either may be NULL) and the exact
+ * totals (sum N, sum J) into totals[2] (host, may be NULL).  Synchronises. */
+mclg_status mclg_moments(mclg_handle h, int32_t *N, int32_t *J, int64_t *totals);
+
+/* Statistics (MCLG_STATS): after every step the new field n(x, t+1) is added,
+ * per replica-local position x and pooled over the replicas, as exact int64
+ * sums s1[x][i] = sum n_i, s2[x][p] = sum n_i n_j for p over (i,j) =
+ * 00 01 02 11 12 22, snb[x][3i+j] = sum n_i(x) n_j(x+1), and as FP32
+ * compensated running means and (co)variances.  Eqs. poisson, Poisson2, corr. */
+mclg_status mclg_stats_reset(mclg_handle h);
+
+/* Read the statistics into host arrays (any may be NULL): s1[L*3], s2[L*6],
+ * snb[L*9] int64; cov32[L*6] the FP32-path covariances of n_i, n_j at x;
+ * cov64[L*6] the same from the exact int64 sums (FP64 only in this final
+ * normalisation); *count = number of samples per position.  Synchronises. */
+mclg_status mclg_stats_read(mclg_handle h, int64_t *s1, int64_t *s2, int64_t *snb, float *cov32,
+                            double *cov64, uint64_t *count);
+
+/* Wait for all enqueued work; returns the sticky device error, if any. */
+mclg_status mclg_sync(mclg_handle h);
+
+/* Current time step of the handle (host-side counter, no synchronisation). */
+uint64_t mclg_time(mclg_handle h);
+
+/* Release every resource of the handle.  NULL-safe. */
+void mclg_destroy(mclg_handle h);
+
+/* Static description of a status code. */
+const char *mclg_status_str(mclg_status s);
+
+/* Philox4x32-10 of the library's device generator on n counters: ctr and out
+ * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For
+ * checking the generator against an independent implementation. */
+mclg_status mclg_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
+                        void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCLG_H */

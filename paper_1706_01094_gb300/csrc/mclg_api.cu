@@ -1,0 +1,761 @@
+// Host side of the C ABI declared in include/mclg.h: handle, layout, modes,
+// autotuner, host Poisson initialisation and the conversions between the ABI
+// field and the device form.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/mclg.h"
+#include "mclg_device.cuh"
+#include "mclg_internal.h"
+
+using namespace mclg;
+
+struct mclg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;  // second stream: plain steps of large replicas beside the persistent kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    mclg_params prm{};
+    uint64_t seed = 0;
+    uint32_t R = 0;
+    std::vector<uint32_t> L;          // ABI order
+    std::vector<uint64_t> abi_off;    // ABI order
+    uint64_t S = 0;                   // sum of L
+    // internal order
+    std::vector<uint32_t> order;      // internal k -> replica id
+    std::vector<uint64_t> rep_off;    // internal k -> node offset
+    std::vector<uint32_t> rep_L;      // internal k -> length
+    uint32_t n_small = 0;             // internal replicas [0, n_small) fit a persistent CTA
+    uint64_t small_chunks = 0;        // chunks of the small replicas (they come first)
+    Layout lay;
+    uint16_t *d_B[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t *d_err = nullptr;
+    unsigned long long *d_totals = nullptr;
+    uint16_t *d_stage = nullptr;      // ABI-layout staging for host transfers
+    int32_t *d_stageNJ = nullptr;
+    uint64_t t = 0;
+    bool has_state = false;
+    uint32_t sticky = 0;              // device error bits seen so far
+    // persistent configuration (autotuned)
+    bool tuned = false;
+    uint32_t p_threads = 256, p_cap = 0;
+    std::vector<Unit> units;
+    Unit *d_units = nullptr;
+    // statistics
+    StatsBuffers st{};
+    uint64_t stats_count = 0;
+};
+
+namespace {
+
+constexpr uint64_t kMaxT = uint64_t(1) << 32;
+
+mclg_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? MCLG_OK : MCLG_ERR_CUDA; }
+
+#define MCLG_CK(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return cuda_fail(_e);    \
+    } while (0)
+
+uint64_t pad8(uint64_t v) { return (v + 7u) & ~uint64_t(7); }
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mclg_status status_from_bits(uint32_t bits)
+{
+    if (bits & kErrOverflow) return MCLG_ERR_OVERFLOW;
+    if (bits & kErrSampler) return MCLG_ERR_SAMPLER;
+    return MCLG_OK;
+}
+
+// Read the device error word after the stream is idle, fold it into the sticky bits.
+mclg_status collect_errors(mclg_ctx *h)
+{
+    MCLG_CK(cudaStreamSynchronize(h->stream));
+    uint32_t bits = 0;
+    MCLG_CK(cudaMemcpy(&bits, h->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
+    h->sticky |= bits;
+    return status_from_bits(h->sticky);
+}
+
+std::vector<Unit> build_units(const mclg_ctx *h, uint32_t cap)
+{
+    std::vector<Unit> out;
+    uint32_t k = 0;
+    while (k < h->n_small) {
+        Unit u{};
+        u.node_begin = h->rep_off[k];
+        u.rep_begin = k;
+        u.rep_end = k;
+        uint64_t nodes = 0;
+        while (k < h->n_small && u.rep_end - u.rep_begin < kMaxUnitReplicas) {
+            const uint64_t need = pad8(h->rep_L[k]);
+            if (nodes + need > cap && nodes > 0) break;
+            nodes += need;
+            ++k;
+            u.rep_end = k;
+        }
+        u.nodes = uint32_t(nodes);
+        out.push_back(u);
+    }
+    return out;
+}
+
+PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t)
+{
+    PlainArgs a{};
+    a.in = in;
+    a.out = out;
+    a.P = h->lay.P;
+    a.chunk_rep = h->lay.d_chunk_rep;
+    a.rep_off = h->lay.d_rep_off;
+    a.rep_L = h->lay.d_rep_L;
+    a.rep_id = h->lay.d_rep_id;
+    a.t = uint32_t(t);
+    a.C = h->prm.C;
+    a.lam_n = h->prm.lambda_num;
+    a.lam_d = h->prm.lambda_den;
+    a.k0 = uint32_t(h->seed);
+    a.k1 = uint32_t(h->seed >> 32);
+    a.err = h->d_err;
+    return a;
+}
+
+bool streaming(const mclg_ctx *h) { return !(h->prm.flags & MCLG_NO_STREAM); }
+
+// One step over internal replicas [k_begin, k_end) with a single plain launch.
+cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t,
+                             uint32_t k_begin, uint32_t k_end, cudaStream_t s)
+{
+    if (k_begin >= k_end) return cudaSuccess;
+    PlainArgs a = plain_args(h, in, out, t);
+    a.g_begin = h->rep_off[k_begin] / 8u;
+    a.g_end = (h->rep_off[k_end - 1] + pad8(h->rep_L[k_end - 1])) / 8u;
+    if (k_end - k_begin == 1) {
+        a.one_off = h->rep_off[k_begin];
+        a.one_L = h->rep_L[k_begin];
+        a.one_rid = h->order[k_begin];
+        return launch_plain(a, true, streaming(h), s);
+    }
+    return launch_plain(a, false, streaming(h), s);
+}
+
+// One step with one plain launch per replica (the per-replica baseline).
+cudaError_t plain_per_replica_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t,
+                                   cudaStream_t s)
+{
+    for (uint32_t k = 0; k < h->R; ++k) {
+        cudaError_t e = plain_batch_step(h, in, out, t, k, k + 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t0,
+                               uint32_t n_steps, const Unit *d_units, uint32_t cap)
+{
+    PersistentArgs a{};
+    a.in = in;
+    a.out = out;
+    a.P = h->lay.P;
+    a.units = d_units;
+    a.rep_off = h->lay.d_rep_off;
+    a.rep_L = h->lay.d_rep_L;
+    a.rep_id = h->lay.d_rep_id;
+    a.cap = cap;
+    a.t0 = uint32_t(t0);
+    a.n_steps = n_steps;
+    a.C = h->prm.C;
+    a.lam_n = h->prm.lambda_num;
+    a.lam_d = h->prm.lambda_den;
+    a.k0 = uint32_t(h->seed);
+    a.k1 = uint32_t(h->seed >> 32);
+    a.err = h->d_err;
+    return a;
+}
+
+// Autotuner: time a few steps of each (threads, capacity) candidate on a
+// scratch output buffer (results are identical for every candidate; only the
+// speed differs) and keep the fastest.
+mclg_status autotune(mclg_ctx *h)
+{
+    h->tuned = true;
+    if (h->n_small == 0) return MCLG_OK;
+    uint32_t max_small = 0;
+    for (uint32_t k = 0; k < h->n_small; ++k) max_small = std::max<uint32_t>(max_small, uint32_t(pad8(h->rep_L[k])));
+    std::vector<uint32_t> caps;
+    for (uint32_t c = 1024; c <= kMaxUnitNodes; c *= 2)
+        if (c >= max_small) caps.push_back(c);
+    const uint32_t threads_list[] = {128, 256, 512};
+    uint16_t *scratch = nullptr;
+    MCLG_CK(cudaMalloc(&scratch, 3 * h->lay.P * sizeof(uint16_t)));
+    cudaEvent_t e0, e1;
+    MCLG_CK(cudaEventCreate(&e0));
+    MCLG_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    uint32_t best_threads = 256, best_cap = caps.empty() ? kMaxUnitNodes : caps.back();
+    const uint32_t probe_steps = 4;
+    for (uint32_t cap : caps) {
+        std::vector<Unit> units = build_units(h, cap);
+        Unit *d_units = nullptr;
+        MCLG_CK(cudaMalloc(&d_units, units.size() * sizeof(Unit)));
+        MCLG_CK(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit),
+                                cudaMemcpyHostToDevice, h->stream));
+        for (uint32_t th : threads_list) {
+            PersistentArgs a = persistent_args(h, h->d_B[h->cur], scratch, h->t, probe_steps,
+                                               d_units, cap);
+            // warm-up, then timed
+            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, streaming(h), h->stream));
+            MCLG_CK(cudaEventRecord(e0, h->stream));
+            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, streaming(h), h->stream));
+            MCLG_CK(cudaEventRecord(e1, h->stream));
+            MCLG_CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            MCLG_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_threads = th;
+                best_cap = cap;
+            }
+        }
+        MCLG_CK(cudaStreamSynchronize(h->stream));
+        cudaFree(d_units);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    // the probes may have flagged errors of the current state; they are the
+    // same errors the real steps will flag, so they are not folded in here
+    MCLG_CK(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
+    h->p_threads = best_threads;
+    h->p_cap = best_cap;
+    h->units = build_units(h, best_cap);
+    if (h->d_units) cudaFree(h->d_units);
+    MCLG_CK(cudaMalloc(&h->d_units, h->units.size() * sizeof(Unit)));
+    MCLG_CK(cudaMemcpyAsync(h->d_units, h->units.data(), h->units.size() * sizeof(Unit),
+                            cudaMemcpyHostToDevice, h->stream));
+    return MCLG_OK;
+}
+
+uint32_t effective_mode(const mclg_ctx *h)
+{
+    if (h->prm.flags & MCLG_STATS) return 3u;  // batched plain: state in HBM after each step
+    if (h->prm.mode == MCLG_MODE_PLAIN) return MCLG_MODE_PLAIN;
+    if (h->prm.mode == MCLG_MODE_PERSISTENT) return MCLG_MODE_PERSISTENT;
+    if (h->prm.mode == 3u) return 3u;
+    // AUTO: a single replica or only large replicas -> plain; else persistent
+    if (h->n_small == 0) return h->R == 1 ? MCLG_MODE_PLAIN : 3u;
+    return MCLG_MODE_PERSISTENT;
+}
+
+// ----------------------------------------------------------- host init ---
+// Entropic equilibrium of Eq. D1Q3equil and Poisson sampling by inversion,
+// evaluated in the operation order fixed by the ABI's initialisation
+// contract (FP64, no contraction).
+void equilibrium(double rho, double u, double f[3])
+{
+    static const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    const double s = std::sqrt(1.0 + 3.0 * u * u) - 1.0;
+    for (int i = 0; i < 3; ++i) {
+        const double v = double(i - 1);
+        f[i] = rho * w[i] * (1.0 + 3.0 * v * u + (3.0 * v * v - 1.0) * s);
+    }
+}
+
+uint32_t poisson_by_inversion(double mu, double U)
+{
+    double pk = std::exp(-mu);
+    double cdf = pk;
+    uint32_t k = 0;
+    while (U >= cdf && k < 200u) {
+        ++k;
+        pk = pk * (mu / double(k));
+        cdf = cdf + pk;
+    }
+    return k;
+}
+
+int init_range(const mclg_ctx *h, const double *rho, const double *u, uint16_t *n, uint32_t r,
+               uint32_t x_begin, uint32_t x_end)
+{
+    const uint32_t k0 = uint32_t(h->seed), k1 = uint32_t(h->seed >> 32);
+    int err = 0;
+    const uint64_t a0 = h->abi_off[r];
+    for (uint32_t x = x_begin; x < x_end; ++x) {
+        const double rh = rho[a0 + x], uu = u[a0 + x];
+        if (!(rh >= 0.0) || !std::isfinite(rh) || !(std::fabs(uu) <= 1.0)) return 8;
+        double f[3];
+        equilibrium(rh, uu, f);
+        for (uint32_t i = 0; i < 3; ++i) {
+            const double mu = f[i] > 0.0 ? f[i] : 0.0;
+            uint32_t parts = uint32_t(std::ceil(mu / 32.0));
+            if (parts < 1) parts = 1;
+            const double part_mu = mu / double(parts);
+            uint64_t total = 0;
+            for (uint32_t q = 0; q < parts; ++q) {
+                uint32_t w0 = x, w1 = r, w2 = q / 2, w3 = (kPurposeInit << 28) | i;
+                philox4x32_10(w0, w1, w2, w3, k0, k1);
+                const uint32_t lo = (q & 1u) ? w2 : w0, hi = (q & 1u) ? w3 : w1;
+                const uint64_t m = ((uint64_t(hi) << 32) | lo) >> 11;
+                const double U = double(m) * (1.0 / 9007199254740992.0);
+                total += poisson_by_inversion(part_mu, U);
+            }
+            if (total > 65535u) {
+                err |= 1;
+                total = 65535u;
+            }
+            n[i * h->S + a0 + x] = uint16_t(total);
+        }
+    }
+    return err;
+}
+
+mclg_status upload_state(mclg_ctx *h, const uint16_t *n, uint64_t t)
+{
+    const bool dev = is_device_ptr(n);
+    const uint16_t *src = n;
+    if (!dev) {
+        MCLG_CK(cudaMemcpyAsync(h->d_stage, n, 3 * h->S * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                h->stream));
+        src = h->d_stage;
+    }
+    MCLG_CK(launch_to_device_form(src, h->S, h->d_B[h->cur], h->lay, streaming(h) ? 1 : 0,
+                                  h->stream));
+    MCLG_CK(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
+    if (!dev) MCLG_CK(cudaStreamSynchronize(h->stream));  // the caller may free n on return
+    h->t = t;
+    h->sticky = 0;
+    h->has_state = true;
+    return MCLG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mclg_default_params(mclg_params *p)
+{
+    if (!p) return;
+    p->C = 10;
+    p->lambda_num = 1;
+    p->lambda_den = 1;
+    p->flags = 0;
+    p->mode = MCLG_MODE_AUTO;
+}
+
+const char *mclg_status_str(mclg_status s)
+{
+    switch (s) {
+    case MCLG_OK: return "ok";
+    case MCLG_ERR_ARG: return "invalid argument";
+    case MCLG_ERR_NOMEM: return "out of memory";
+    case MCLG_ERR_CUDA: return "CUDA runtime error";
+    case MCLG_ERR_OVERFLOW: return "occupation overflow (uint16)";
+    case MCLG_ERR_TIMEOUT: return "device wait timed out";
+    case MCLG_ERR_STATE: return "no state set";
+    case MCLG_ERR_SAMPLER: return "sampler refinement cap reached";
+    }
+    return "unknown status";
+}
+
+void mclg_destroy(mclg_handle h)
+{
+    if (!h) return;
+    if (h->stream || h->d_err) cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    cudaFree(h->d_B[0]);
+    cudaFree(h->d_B[1]);
+    cudaFree(h->d_err);
+    cudaFree(h->d_totals);
+    cudaFree(h->d_stage);
+    cudaFree(h->d_stageNJ);
+    cudaFree(h->d_units);
+    cudaFree(h->lay.d_abi_off);
+    cudaFree(h->lay.d_rep_off);
+    cudaFree(h->lay.d_rep_L);
+    cudaFree(h->lay.d_rep_id);
+    cudaFree(h->lay.d_chunk_rep);
+    cudaFree(h->st.s1);
+    cudaFree(h->st.s2);
+    cudaFree(h->st.snb);
+    cudaFree(h->st.mean32);
+    cudaFree(h->st.mean32c);
+    cudaFree(h->st.m2);
+    cudaFree(h->st.m2c);
+    cudaFree(h->st.count);
+    delete h;
+}
+
+mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, const mclg_params *p,
+                        void *cuda_stream, mclg_handle *out)
+{
+    if (!out) return MCLG_ERR_ARG;
+    *out = nullptr;
+    if (!L || replicas == 0) return MCLG_ERR_ARG;
+    mclg_params prm;
+    mclg_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.lambda_den < 1 || prm.lambda_den > 256 || prm.lambda_num > prm.lambda_den) return MCLG_ERR_ARG;
+    if (prm.mode > 3u || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS))) return MCLG_ERR_ARG;
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < replicas; ++r) {
+        if (L[r] == 0 || L[r] > (uint32_t(1) << 31)) return MCLG_ERR_ARG;
+        S += L[r];
+    }
+    if (S >= (uint64_t(1) << 40)) return MCLG_ERR_ARG;
+    if (prm.flags & MCLG_STATS)
+        for (uint32_t r = 1; r < replicas; ++r)
+            if (L[r] != L[0]) return MCLG_ERR_ARG;
+
+    mclg_ctx *h = new (std::nothrow) mclg_ctx();
+    if (!h) return MCLG_ERR_NOMEM;
+    h->prm = prm;
+    h->seed = seed;
+    h->R = replicas;
+    h->L.assign(L, L + replicas);
+    h->S = S;
+    h->abi_off.resize(replicas);
+    uint64_t acc = 0;
+    for (uint32_t r = 0; r < replicas; ++r) {
+        h->abi_off[r] = acc;
+        acc += L[r];
+    }
+    // internal order: replicas that fit a persistent CTA first (ABI order
+    // within each group); with statistics the ABI order is kept so that the
+    // pooled positions line up with a fixed stride
+    const bool keep_order = (prm.flags & MCLG_STATS) != 0;
+    for (uint32_t r = 0; r < replicas; ++r)
+        if (keep_order || pad8(L[r]) <= kMaxUnitNodes) h->order.push_back(r);
+    h->n_small = 0;
+    for (uint32_t r : h->order)
+        if (pad8(L[r]) <= kMaxUnitNodes) ++h->n_small;
+    if (keep_order) h->n_small = 0;
+    if (!keep_order)
+        for (uint32_t r = 0; r < replicas; ++r)
+            if (pad8(L[r]) > kMaxUnitNodes) h->order.push_back(r);
+    h->rep_off.resize(replicas);
+    h->rep_L.resize(replicas);
+    uint64_t off = 0;
+    for (uint32_t k = 0; k < replicas; ++k) {
+        h->rep_off[k] = off;
+        h->rep_L[k] = L[h->order[k]];
+        off += pad8(h->rep_L[k]);
+    }
+    h->lay.P = off;
+    h->small_chunks = h->n_small ? (h->rep_off[h->n_small - 1] + pad8(h->rep_L[h->n_small - 1])) / 8 : 0;
+    std::vector<uint32_t> chunk_rep(off / 8);
+    for (uint32_t k = 0; k < replicas; ++k)
+        for (uint64_t g = h->rep_off[k] / 8; g < (h->rep_off[k] + pad8(h->rep_L[k])) / 8; ++g)
+            chunk_rep[g] = k;
+
+    mclg_status st = MCLG_OK;
+    auto fail = [&](mclg_status s) {
+        mclg_destroy(h);
+        return s;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(MCLG_ERR_CUDA);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess) return fail(MCLG_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(MCLG_ERR_CUDA);
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    };
+    const size_t planes = 3 * h->lay.P * sizeof(uint16_t);
+    if (!alloc((void **)&h->d_B[0], planes) || !alloc((void **)&h->d_B[1], planes) ||
+        !alloc((void **)&h->d_err, sizeof(uint32_t)) ||
+        !alloc((void **)&h->d_totals, 2 * sizeof(unsigned long long)) ||
+        !alloc((void **)&h->d_stage, 3 * S * sizeof(uint16_t)) ||
+        !alloc((void **)&h->lay.d_abi_off, replicas * sizeof(uint64_t)) ||
+        !alloc((void **)&h->lay.d_rep_off, replicas * sizeof(uint64_t)) ||
+        !alloc((void **)&h->lay.d_rep_L, replicas * sizeof(uint32_t)) ||
+        !alloc((void **)&h->lay.d_rep_id, replicas * sizeof(uint32_t)) ||
+        !alloc((void **)&h->lay.d_chunk_rep, chunk_rep.size() * sizeof(uint32_t)))
+        return fail(MCLG_ERR_NOMEM);
+    if (cudaMemcpy(h->lay.d_abi_off, h->abi_off.data(), replicas * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->lay.d_rep_off, h->rep_off.data(), replicas * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->lay.d_rep_L, h->rep_L.data(), replicas * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->lay.d_rep_id, h->order.data(), replicas * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->lay.d_chunk_rep, chunk_rep.data(), chunk_rep.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->d_err, 0, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(h->d_B[0], 0, planes) != cudaSuccess || cudaMemset(h->d_B[1], 0, planes) != cudaSuccess)
+        return fail(MCLG_ERR_CUDA);
+    if (prm.flags & MCLG_STATS) {
+        const uint32_t Lc = L[0];
+        if (!alloc((void **)&h->st.s1, Lc * 3 * sizeof(long long)) ||
+            !alloc((void **)&h->st.s2, Lc * 6 * sizeof(long long)) ||
+            !alloc((void **)&h->st.snb, Lc * 9 * sizeof(long long)) ||
+            !alloc((void **)&h->st.mean32, Lc * 3 * sizeof(float)) ||
+            !alloc((void **)&h->st.mean32c, Lc * 3 * sizeof(float)) ||
+            !alloc((void **)&h->st.m2, Lc * 6 * sizeof(float)) ||
+            !alloc((void **)&h->st.m2c, Lc * 6 * sizeof(float)) ||
+            !alloc((void **)&h->st.count, sizeof(unsigned long long)))
+            return fail(MCLG_ERR_NOMEM);
+        *out = h;
+        st = mclg_stats_reset(h);
+        if (st != MCLG_OK) {
+            *out = nullptr;
+            return fail(st);
+        }
+    }
+    *out = h;
+    return MCLG_OK;
+}
+
+mclg_status mclg_set_state(mclg_handle h, const uint16_t *n, uint64_t t)
+{
+    if (!h || !n || t >= kMaxT) return MCLG_ERR_ARG;
+    MCLG_CK(cudaSetDevice(h->device));
+    return upload_state(h, n, t);
+}
+
+mclg_status mclg_init(mclg_handle h, const double *rho, const double *u)
+{
+    if (!h || !rho || !u) return MCLG_ERR_ARG;
+    MCLG_CK(cudaSetDevice(h->device));
+    std::vector<uint16_t> n;
+    try {
+        n.resize(3 * h->S);
+    } catch (...) {
+        return MCLG_ERR_NOMEM;
+    }
+    // split the nodes into ranges of at most 64K nodes, spread over the host cores
+    struct Task { uint32_t r, xb, xe; };
+    std::vector<Task> tasks;
+    for (uint32_t r = 0; r < h->R; ++r)
+        for (uint32_t xb = 0; xb < h->L[r]; xb += 65536u)
+            tasks.push_back({r, xb, std::min<uint32_t>(h->L[r], xb + 65536u)});
+    unsigned nth = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
+    nth = std::min<unsigned>(nth, unsigned(tasks.size()));
+    std::vector<int> errs(nth, 0);
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < nth; ++w)
+        pool.emplace_back([&, w]() {
+            for (size_t i = w; i < tasks.size(); i += nth)
+                errs[w] |= init_range(h, rho, u, n.data(), tasks[i].r, tasks[i].xb, tasks[i].xe);
+        });
+    for (auto &th : pool) th.join();
+    int err = 0;
+    for (int e : errs) err |= e;
+    if (err & 8) return MCLG_ERR_ARG;
+    mclg_status s = upload_state(h, n.data(), 0);
+    if (s != MCLG_OK) return s;
+    if (err & 1) {
+        h->sticky |= kErrOverflow;
+        return MCLG_ERR_OVERFLOW;
+    }
+    return MCLG_OK;
+}
+
+mclg_status mclg_get_state(mclg_handle h, uint16_t *n, uint64_t *t)
+{
+    if (!h || !n) return MCLG_ERR_ARG;
+    if (!h->has_state) return MCLG_ERR_STATE;
+    MCLG_CK(cudaSetDevice(h->device));
+    const bool dev = is_device_ptr(n);
+    uint16_t *dst = dev ? n : h->d_stage;
+    MCLG_CK(launch_from_device_form(h->d_B[h->cur], dst, h->S, h->lay, streaming(h) ? 1 : 0, h->stream));
+    if (!dev)
+        MCLG_CK(cudaMemcpyAsync(n, h->d_stage, 3 * h->S * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                h->stream));
+    if (t) *t = h->t;
+    return collect_errors(h);
+}
+
+mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
+{
+    if (!h) return MCLG_ERR_ARG;
+    if (!h->has_state) return MCLG_ERR_STATE;
+    if (h->t + n_steps > kMaxT) return MCLG_ERR_ARG;
+    if (h->sticky) return status_from_bits(h->sticky);
+    if (n_steps == 0) return MCLG_OK;
+    MCLG_CK(cudaSetDevice(h->device));
+    const uint32_t mode = effective_mode(h);
+    if (mode == MCLG_MODE_PLAIN || mode == 3u) {
+        for (uint64_t s = 0; s < n_steps; ++s) {
+            const uint16_t *in = h->d_B[h->cur];
+            uint16_t *outb = h->d_B[h->cur ^ 1];
+            if (mode == MCLG_MODE_PLAIN)
+                MCLG_CK(plain_per_replica_step(h, in, outb, h->t, h->stream));
+            else
+                MCLG_CK(plain_batch_step(h, in, outb, h->t, 0, h->R, h->stream));
+            h->cur ^= 1;
+            h->t += 1;
+            if (h->prm.flags & MCLG_STATS) {
+                MCLG_CK(launch_stats(h->d_B[h->cur], h->lay.P, h->L[0], h->R, pad8(h->L[0]),
+                                     streaming(h) ? 1 : 0, h->st, h->stream));
+                h->stats_count += h->R;
+            }
+        }
+        return MCLG_OK;
+    }
+    // persistent: small replicas stay on chip for all n_steps (chunks of at
+    // most 2^16 steps per launch); large replicas step beside them on the aux
+    // stream with one batched plain launch per step
+    if (!h->tuned) {
+        mclg_status s = autotune(h);
+        if (s != MCLG_OK) return s;
+    }
+    const int start = h->cur;
+    const int final_buf = int((uint64_t(start) + n_steps) & 1u);
+    MCLG_CK(cudaEventRecord(h->ev_fork, h->stream));
+    if (h->n_small < h->R) {
+        MCLG_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        int c = start;
+        for (uint64_t s = 0; s < n_steps; ++s) {
+            MCLG_CK(plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], h->t + s, h->n_small, h->R, h->aux));
+            c ^= 1;
+        }
+        MCLG_CK(cudaEventRecord(h->ev_join, h->aux));
+    }
+    // Each CTA reads its own unit into shared memory before it writes the unit
+    // back, and units do not overlap, so launches after the first work in place.
+    uint64_t done = 0;
+    const uint16_t *in = h->d_B[start];
+    uint16_t *outb = h->d_B[final_buf];
+    while (done < n_steps) {
+        const uint32_t chunk = uint32_t(std::min<uint64_t>(n_steps - done, 65536u));
+        PersistentArgs a = persistent_args(h, in, outb, h->t + done, chunk, h->d_units, h->p_cap);
+        MCLG_CK(launch_persistent(a, uint32_t(h->units.size()), h->p_threads, streaming(h), h->stream));
+        in = outb;
+        done += chunk;
+    }
+    if (h->n_small < h->R) MCLG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    h->cur = final_buf;
+    h->t += n_steps;
+    return MCLG_OK;
+}
+
+mclg_status mclg_moments(mclg_handle h, int32_t *N, int32_t *J, int64_t *totals)
+{
+    if (!h) return MCLG_ERR_ARG;
+    if (!h->has_state) return MCLG_ERR_STATE;
+    MCLG_CK(cudaSetDevice(h->device));
+    const bool devN = N && is_device_ptr(N), devJ = J && is_device_ptr(J);
+    if ((N && !devN) || (J && !devJ)) {
+        if (!h->d_stageNJ && cudaMalloc(&h->d_stageNJ, 2 * h->S * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return MCLG_ERR_NOMEM;
+        }
+    }
+    int32_t *dN = N ? (devN ? N : h->d_stageNJ) : nullptr;
+    int32_t *dJ = J ? (devJ ? J : h->d_stageNJ + h->S) : nullptr;
+    MCLG_CK(cudaMemsetAsync(h->d_totals, 0, 2 * sizeof(unsigned long long), h->stream));
+    MCLG_CK(launch_moments(h->d_B[h->cur], dN, dJ, h->lay, streaming(h) ? 1 : 0, h->d_totals, h->stream));
+    if (N && !devN)
+        MCLG_CK(cudaMemcpyAsync(N, dN, h->S * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    if (J && !devJ)
+        MCLG_CK(cudaMemcpyAsync(J, dJ, h->S * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    unsigned long long tot[2] = {0, 0};
+    MCLG_CK(cudaMemcpyAsync(tot, h->d_totals, sizeof(tot), cudaMemcpyDeviceToHost, h->stream));
+    mclg_status s = collect_errors(h);
+    if (totals) {
+        totals[0] = (int64_t)tot[0];
+        totals[1] = (int64_t)tot[1];
+    }
+    return s;
+}
+
+mclg_status mclg_stats_reset(mclg_handle h)
+{
+    if (!h) return MCLG_ERR_ARG;
+    if (!(h->prm.flags & MCLG_STATS)) return MCLG_ERR_ARG;
+    MCLG_CK(cudaSetDevice(h->device));
+    const size_t Lc = h->L[0];
+    MCLG_CK(cudaMemsetAsync(h->st.s1, 0, Lc * 3 * sizeof(long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.s2, 0, Lc * 6 * sizeof(long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.snb, 0, Lc * 9 * sizeof(long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.mean32, 0, Lc * 3 * sizeof(float), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.mean32c, 0, Lc * 3 * sizeof(float), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.m2, 0, Lc * 6 * sizeof(float), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.m2c, 0, Lc * 6 * sizeof(float), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.count, 0, sizeof(unsigned long long), h->stream));
+    h->stats_count = 0;
+    return MCLG_OK;
+}
+
+mclg_status mclg_stats_read(mclg_handle h, int64_t *s1, int64_t *s2, int64_t *snb, float *cov32,
+                            double *cov64, uint64_t *count)
+{
+    if (!h) return MCLG_ERR_ARG;
+    if (!(h->prm.flags & MCLG_STATS)) return MCLG_ERR_ARG;
+    MCLG_CK(cudaSetDevice(h->device));
+    const size_t Lc = h->L[0];
+    std::vector<long long> a1(Lc * 3), a2(Lc * 6), anb(Lc * 9);
+    std::vector<float> m2(Lc * 6);
+    unsigned long long cnt = 0;
+    MCLG_CK(cudaMemcpyAsync(a1.data(), h->st.s1, a1.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    MCLG_CK(cudaMemcpyAsync(a2.data(), h->st.s2, a2.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    MCLG_CK(cudaMemcpyAsync(anb.data(), h->st.snb, anb.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    MCLG_CK(cudaMemcpyAsync(m2.data(), h->st.m2, m2.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    MCLG_CK(cudaMemcpyAsync(&cnt, h->st.count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    mclg_status s = collect_errors(h);
+    if (s1) std::memcpy(s1, a1.data(), a1.size() * sizeof(int64_t));
+    if (s2) std::memcpy(s2, a2.data(), a2.size() * sizeof(int64_t));
+    if (snb) std::memcpy(snb, anb.data(), anb.size() * sizeof(int64_t));
+    static const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    for (size_t x = 0; x < Lc; ++x)
+        for (int q = 0; q < 6; ++q) {
+            if (cov32) cov32[6 * x + q] = cnt ? m2[6 * x + q] / float(cnt) : 0.0f;
+            if (cov64) {
+                if (!cnt) {
+                    cov64[6 * x + q] = 0.0;
+                    continue;
+                }
+                const __int128 num = (__int128)cnt * a2[6 * x + q] -
+                                     (__int128)a1[3 * x + pi[q]] * a1[3 * x + pj[q]];
+                cov64[6 * x + q] = double((long double)num / ((long double)cnt * (long double)cnt));
+            }
+        }
+    if (count) *count = cnt;
+    return s;
+}
+
+mclg_status mclg_sync(mclg_handle h)
+{
+    if (!h) return MCLG_ERR_ARG;
+    MCLG_CK(cudaSetDevice(h->device));
+    return collect_errors(h);
+}
+
+uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
+
+mclg_status mclg_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out, void *cuda_stream)
+{
+    if ((!ctr || !out) && n) return MCLG_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    MCLG_CK(launch_philox(ctr, n, uint32_t(seed), uint32_t(seed >> 32), out, s));
+    MCLG_CK(cudaStreamSynchronize(s));
+    return MCLG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Device building blocks of the D1Q3 MCLG step: Philox4x32-10 in registers and
+// the exact integer sampler of one sub-collision (Sec. III, Sec. III.A).
+#pragma once
+#include <cstdint>
+
+#ifndef MCLG_HD
+#define MCLG_HD __host__ __device__ __forceinline__
+#endif
+
+namespace mclg {
+
+constexpr uint32_t kPurposeCollide = 0u;
+constexpr uint32_t kPurposeRefine = 1u;
+constexpr uint32_t kPurposeInit = 2u;
+constexpr int kChunksPerBlock = 10;  // 12-bit primary chunks in one 128-bit Philox block
+constexpr int kMaxRefine = 4;        // 16-bit refinement chunks allowed per decision
+
+constexpr uint32_t kErrOverflow = 1u;
+constexpr uint32_t kErrSampler = 2u;
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds; each multiplies words 0 and
+// 2 by the two round constants, swaps the halves and xors in the round key;
+// the key advances by the Weyl increments between rounds.
+MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3, uint32_t k0,
+                           uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+#else
+        const uint64_t p0 = uint64_t(0xD2511F53u) * x0, p1 = uint64_t(0xCD9E8D57u) * x2;
+        const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+        const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+#endif
+        const uint32_t y0 = hi1 ^ x1 ^ k0;
+        const uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+}
+
+// Bits [12m, 12m + 12) of the 128-bit block (w0 least significant), m in 0..9.
+template <int m>
+__device__ __forceinline__ uint32_t chunk12(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3)
+{
+    constexpr int off = 12 * m, word = off / 32, sh = off % 32;
+    const uint32_t w[4] = {w0, w1, w2, w3};
+    if constexpr (sh + 12 <= 32) {
+        return (w[word] >> sh) & 0xFFFu;
+    } else {
+        return __funnelshift_r(w[word], w[word + 1], sh) & 0xFFFu;
+    }
+}
+
+struct NodeKey {
+    uint32_t x, r, t, k0, k1;
+};
+
+// Refinement chunk s of the node-step: bits [16(s%8), 16(s%8)+16) of block
+// (x, r, t, kPurposeRefine << 28 | s/8).
+__device__ __forceinline__ uint32_t refine_chunk(const NodeKey &nk, uint32_t s)
+{
+    uint32_t w0 = nk.x, w1 = nk.r, w2 = nk.t, w3 = (kPurposeRefine << 28) | (s >> 3);
+    philox4x32_10(w0, w1, w2, w3, nk.k0, nk.k1);
+    const uint32_t m = s & 7u;
+    const uint32_t word = (m >> 1) == 0 ? w0 : (m >> 1) == 1 ? w1 : (m >> 1) == 2 ? w2 : w3;
+    return (word >> ((m & 1u) * 16u)) & 0xFFFFu;
+}
+
+// Finish a decision whose 12-bit primary chunk left U's region open.
+// R1 = T1 * 2^12 - q D and R2 = T2 * 2^12 - q D (signed): with `bits` bits of U
+// known, U*D*2^bits - T*2^bits lies in [-R, D - R), so R >= D means U < T/D
+// for certain and R <= 0 means U >= T/D for certain.  A resolved remainder is
+// clamped to 0 or D (it stays resolved under R <- R 2^16 - q D) which keeps
+// |R| 2^16 < 2^63 for D < 2^47.  Returns the region (0, 1, 2) or 3 when the
+// refinement cap is reached.
+static __device__ __noinline__ uint32_t refine_decision(int64_t R1, int64_t R2, int64_t D,
+                                                 const NodeKey &nk, uint32_t &next_ref)
+{
+    for (int k = 0; k < kMaxRefine; ++k) {
+        R1 = R1 >= D ? D : (R1 <= 0 ? 0 : R1);
+        R2 = R2 >= D ? D : (R2 <= 0 ? 0 : R2);
+        const int64_t q = int64_t(refine_chunk(nk, next_ref));
+        ++next_ref;
+        R1 = R1 * 65536 - q * D;
+        R2 = R2 * 65536 - q * D;
+        if (R1 >= D) return 0u;
+        if (R1 <= 0 && R2 >= D) return 1u;
+        if (R2 <= 0) return 2u;
+    }
+    return 3u;
+}
+
+// C sequential sub-collisions at one node.  (a, b, c) = (n_-1, n_0, n_+1),
+// all <= 65535 on entry; on return the post-collision state.  Error bits go
+// to err (the node stops at the first error).
+template <bool kLambdaOne>
+__device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t &c,
+                                             const NodeKey &nk, uint32_t C, uint32_t lam_n,
+                                             uint32_t lam_d, uint32_t &err)
+{
+    const uint32_t N = a + b + c;
+    if (N < 2u) return;
+    const uint64_t D = kLambdaOne ? 8ull * N * N : 8ull * N * N * lam_d;
+    uint32_t next_ref = 0;
+    for (uint32_t blk = 0; blk * kChunksPerBlock < C; ++blk) {
+        uint32_t w0 = nk.x, w1 = nk.r, w2 = nk.t, w3 = (kPurposeCollide << 28) | blk;
+        philox4x32_10(w0, w1, w2, w3, nk.k0, nk.k1);
+        const uint32_t base = blk * kChunksPerBlock;
+        uint32_t q[kChunksPerBlock];
+        q[0] = chunk12<0>(w0, w1, w2, w3);
+        q[1] = chunk12<1>(w0, w1, w2, w3);
+        q[2] = chunk12<2>(w0, w1, w2, w3);
+        q[3] = chunk12<3>(w0, w1, w2, w3);
+        q[4] = chunk12<4>(w0, w1, w2, w3);
+        q[5] = chunk12<5>(w0, w1, w2, w3);
+        q[6] = chunk12<6>(w0, w1, w2, w3);
+        q[7] = chunk12<7>(w0, w1, w2, w3);
+        q[8] = chunk12<8>(w0, w1, w2, w3);
+        q[9] = chunk12<9>(w0, w1, w2, w3);
+#pragma unroll
+        for (int m = 0; m < kChunksPerBlock; ++m) {
+            if (base + m >= C) break;
+            const uint64_t ac = uint64_t(a * c);          // < 2^32
+            const uint64_t bb = uint64_t(b * (b - 1u));   // b(b-1) < 2^32, 0 for b = 0
+            const uint64_t T1 = kLambdaOne ? ac << 4 : (ac << 4) * lam_n;
+            const uint64_t T2 = T1 + (kLambdaOne ? bb : bb * lam_n);
+            const uint64_t X = uint64_t(q[m]) * D;
+            const uint64_t S1 = T1 << 12, S2 = T2 << 12;
+            uint32_t region;
+            if (X + D <= S1) {
+                region = 0u;
+            } else if (X >= S1 && X + D <= S2) {
+                region = 1u;
+            } else if (X >= S2) {
+                region = 2u;
+            } else {
+                region = refine_decision(int64_t(S1 - X), int64_t(S2 - X), int64_t(D), nk,
+                                         next_ref);
+                if (region == 3u) {
+                    err |= kErrSampler;
+                    return;
+                }
+            }
+            if (region == 0u) {  // {-1, +1} -> {0, 0}
+                if (b + 2u > 65535u) {
+                    err |= kErrOverflow;
+                    return;
+                }
+                a -= 1u;
+                b += 2u;
+                c -= 1u;
+            } else if (region == 1u) {  // {0, 0} -> {-1, +1}
+                if (a + 1u > 65535u || c + 1u > 65535u) {
+                    err |= kErrOverflow;
+                    return;
+                }
+                a += 1u;
+                b -= 2u;
+                c += 1u;
+            }
+        }
+    }
+}
+
+}  // namespace mclg

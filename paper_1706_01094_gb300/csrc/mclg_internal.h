@@ -1,0 +1,80 @@
+// Internal declarations shared by the library's translation units (not part
+// of the public C ABI in include/mclg.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mclg {
+
+constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain kernel
+constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CTA size
+constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
+constexpr uint32_t kMaxUnitNodes = 16384;        // shared-memory capacity of a persistent CTA
+
+// Device-resident description of the internal replica order.
+struct Layout {
+    uint64_t P = 0;                   // padded nodes per plane (multiple of 8)
+    uint64_t *d_abi_off = nullptr;    // [R] ABI offset of replica id r (prefix sum of L)
+    uint64_t *d_rep_off = nullptr;    // [R] internal offset of internal replica k
+    uint32_t *d_rep_L = nullptr;      // [R] length of internal replica k
+    uint32_t *d_rep_id = nullptr;     // [R] replica id r (ABI index, RNG key) of internal k
+    uint32_t *d_chunk_rep = nullptr;  // [P/8] internal replica of each 8-node chunk
+};
+
+struct PlainArgs {
+    const uint16_t *in;
+    uint16_t *out;
+    uint64_t P;
+    uint64_t g_begin, g_end;  // chunk range (whole replicas)
+    const uint32_t *chunk_rep;
+    const uint64_t *rep_off;
+    const uint32_t *rep_L;
+    const uint32_t *rep_id;
+    uint64_t one_off;  // single-replica launch: offset, length, id
+    uint32_t one_L, one_rid;
+    uint32_t t, C, lam_n, lam_d, k0, k1;
+    uint32_t *err;
+};
+
+struct Unit {
+    uint64_t node_begin;  // internal node offset of the unit's first replica
+    uint32_t nodes;       // padded nodes in the unit
+    uint32_t rep_begin, rep_end;  // internal replica range
+};
+
+struct PersistentArgs {
+    const uint16_t *in;
+    uint16_t *out;
+    uint64_t P;
+    const Unit *units;
+    const uint64_t *rep_off;
+    const uint32_t *rep_L;
+    const uint32_t *rep_id;
+    uint32_t cap;  // shared-memory nodes per buffer (>= every unit's nodes)
+    uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
+    uint32_t *err;
+};
+
+struct StatsBuffers {
+    long long *s1, *s2, *snb;   // [L*3], [L*6], [L*9]
+    float *mean32, *mean32c;    // [L*3] running means and their compensation
+    float *m2, *m2c;            // [L*6] running co-moments and their compensation
+    unsigned long long *count;  // samples per position
+};
+
+cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s);
+size_t persistent_smem_bytes(uint32_t cap);
+cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
+                              bool stream, cudaStream_t s);
+cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,
+                                  int stream, cudaStream_t s);
+cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,
+                                    int stream, cudaStream_t s);
+cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
+                           unsigned long long *totals, cudaStream_t s);
+cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
+                         int stream, const StatsBuffers &st, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint32_t *out,
+                          cudaStream_t s);
+
+}  // namespace mclg

@@ -1,0 +1,483 @@
+// sm_103a kernels of the D1Q3 Monte Carlo Lattice Gas time step (Sec. III).
+//
+// Device state layout ("pre-streamed" form).  Each of the three planes
+// (v = -1, 0, +1) is a uint16 array of P nodes; replica k of the internal
+// order occupies [off_k, off_k + L_k) with off_k a multiple of 8 (16-byte
+// aligned vectors), padding nodes hold 0.  A buffer B holds the occupations
+// one streaming step *before* the canonical pre-collision field: the field of
+// the paper's evolution equation is n_i(x, t) = B_i(x - v_i), i.e.
+//     n_-1(x) = B_-1(x + 1),  n_0(x) = B_0(x),  n_+1(x) = B_+1(x - 1)
+// (periodic).  One time step is then a pull: read the three streamed values
+// of node x, run the C sub-collisions of time t, write the post-collision
+// values back to node x of the other buffer.  Every read is a coalesced
+// vector load plus two halo values per warp, every write an aligned vector
+// store.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "mclg_device.cuh"
+#include "mclg_internal.h"
+
+namespace mclg {
+
+__device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
+__device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
+
+__device__ __forceinline__ void unpack8(const uint4 v, uint32_t e[8])
+{
+    e[0] = lo16(v.x); e[1] = hi16(v.x);
+    e[2] = lo16(v.y); e[3] = hi16(v.y);
+    e[4] = lo16(v.z); e[5] = hi16(v.z);
+    e[6] = lo16(v.w); e[7] = hi16(v.w);
+}
+
+__device__ __forceinline__ uint4 pack8(const uint32_t e[8])
+{
+    return make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                      e[6] | (e[7] << 16));
+}
+
+__device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
+{
+    if (bits) atomicOr(err, bits);
+}
+
+// ---------------------------------------------------------------------------
+// Plain kernel: one thread per 8-node chunk, any set of whole replicas laid
+// out contiguously (chunk range [g_begin, g_end)).  kOne: a single replica
+// whose offset, length and id come from the arguments (no table reads).
+// ---------------------------------------------------------------------------
+template <bool kOne, bool kStream, bool kLambdaOne>
+__global__ void __launch_bounds__(kPlainThreads)
+    k_step_plain(PlainArgs p)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t g = p.g_begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool active = g < p.g_end;
+
+    uint64_t off;
+    uint32_t L, rid;
+    if (kOne) {
+        off = p.one_off;
+        L = p.one_L;
+        rid = p.one_rid;
+    } else {
+        const uint32_t k = active ? p.chunk_rep[g] : p.chunk_rep[p.g_end - 1];
+        off = p.rep_off[k];
+        L = p.rep_L[k];
+        rid = p.rep_id[k];
+    }
+    const uint64_t node0 = (active ? g : p.g_end - 1) * 8u;  // first node of the chunk
+    const uint32_t x0 = uint32_t(node0 - off);                 // replica-local
+
+    const uint16_t *__restrict__ inm = p.in;
+    const uint16_t *__restrict__ in0 = p.in + p.P;
+    const uint16_t *__restrict__ inp = p.in + 2 * p.P;
+
+    const uint4 vm = __ldcs(reinterpret_cast<const uint4 *>(inm + node0));
+    const uint4 v0 = __ldcs(reinterpret_cast<const uint4 *>(in0 + node0));
+    const uint4 vp = __ldcs(reinterpret_cast<const uint4 *>(inp + node0));
+
+    uint32_t em[8], e0[8], ep[8];
+    unpack8(vm, em);
+    unpack8(v0, e0);
+    unpack8(vp, ep);
+
+    // Halo: the v = -1 value right of the chunk and the v = +1 value left of it.
+    uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
+    uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[7], 1);
+    if (kStream) {
+        if (!(lane < 31u && x0 + 8u < L)) nxt = inm[off + (x0 + 8u < L ? x0 + 8u : 0u)];
+        if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
+    }
+    const uint32_t e = L - x0 < 8u ? L - x0 : 8u;  // valid nodes in this chunk
+
+    uint32_t err = 0;
+    uint32_t om[8], o0[8], op[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t a, b, c;
+        if (kStream) {
+            a = (uint32_t(j) + 1u < e) ? em[(j + 1) & 7] : nxt;
+            b = e0[j];
+            c = (j > 0) ? ep[(j + 7) & 7] : prv;
+        } else {
+            a = em[j];
+            b = e0[j];
+            c = ep[j];
+        }
+        if (uint32_t(j) < e) {
+            const NodeKey nk{x0 + uint32_t(j), rid, p.t, p.k0, p.k1};
+            collide_node<kLambdaOne>(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+        } else {
+            a = b = c = 0u;
+        }
+        om[j] = a;
+        o0[j] = b;
+        op[j] = c;
+    }
+    if (active) {
+        __stcs(reinterpret_cast<uint4 *>(p.out + node0), pack8(om));
+        __stcs(reinterpret_cast<uint4 *>(p.out + p.P + node0), pack8(o0));
+        __stcs(reinterpret_cast<uint4 *>(p.out + 2 * p.P + node0), pack8(op));
+        flag_error(p.err, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel: one CTA per work unit (a run of whole replicas of at most
+// `cap` padded nodes), held in shared memory for all n_steps steps.  Two
+// shared buffers alternate; one barrier per step.
+// ---------------------------------------------------------------------------
+template <bool kStream, bool kLambdaOne>
+__global__ void __launch_bounds__(kPersistentMaxThreads) k_step_persistent(PersistentArgs p)
+{
+    extern __shared__ __align__(16) uint16_t smem[];
+    __shared__ uint32_t s_lo[kMaxUnitReplicas + 1];  // unit-local replica starts
+    __shared__ uint32_t s_L[kMaxUnitReplicas];
+    __shared__ uint32_t s_rid[kMaxUnitReplicas];
+
+    const Unit u = p.units[blockIdx.x];
+    const uint32_t nn = u.nodes;  // padded nodes of this unit (multiple of 8)
+    const uint32_t nrep = u.rep_end - u.rep_begin;
+    for (uint32_t k = threadIdx.x; k < nrep; k += blockDim.x) {
+        const uint32_t kk = u.rep_begin + k;
+        s_lo[k] = uint32_t(p.rep_off[kk] - u.node_begin);
+        s_L[k] = p.rep_L[kk];
+        s_rid[k] = p.rep_id[kk];
+    }
+    if (threadIdx.x == 0) s_lo[nrep] = nn;
+
+    uint16_t *buf[2] = {smem, smem + 3 * size_t(p.cap)};
+    // Load the unit: 3 planes x nn nodes, 16-byte vectors.
+    for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
+        const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
+        const uint4 val = *reinterpret_cast<const uint4 *>(p.in + plane * p.P + u.node_begin +
+                                                           8u * w);
+        *reinterpret_cast<uint4 *>(buf[0] + plane * p.cap + 8u * w) = val;
+    }
+    __syncthreads();
+
+    uint32_t err = 0;
+    int cur = 0;
+    for (uint32_t s = 0; s < p.n_steps; ++s) {
+        const uint32_t t = p.t0 + s;
+        const uint16_t *bm = buf[cur], *b0 = buf[cur] + p.cap, *bp = buf[cur] + 2 * p.cap;
+        uint16_t *om = buf[cur ^ 1], *o0 = buf[cur ^ 1] + p.cap, *op = buf[cur ^ 1] + 2 * p.cap;
+        for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
+            // replica of node i: largest k with s_lo[k] <= i
+            uint32_t lo = 0, hi = nrep;
+            while (hi - lo > 1u) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_lo[mid] <= i) lo = mid; else hi = mid;
+            }
+            const uint32_t base = s_lo[lo], L = s_L[lo], x = i - base;
+            uint32_t a = 0, b = 0, c = 0;
+            if (x < L) {
+                if (kStream) {
+                    a = bm[base + (x + 1u < L ? x + 1u : 0u)];
+                    b = b0[i];
+                    c = bp[base + (x > 0u ? x - 1u : L - 1u)];
+                } else {
+                    a = bm[i];
+                    b = b0[i];
+                    c = bp[i];
+                }
+                const NodeKey nk{x, s_rid[lo], t, p.k0, p.k1};
+                collide_node<kLambdaOne>(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+            }
+            om[i] = uint16_t(a);
+            o0[i] = uint16_t(b);
+            op[i] = uint16_t(c);
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
+    for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
+        const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
+        const uint4 val = *reinterpret_cast<const uint4 *>(buf[cur] + plane * p.cap + 8u * w);
+        *reinterpret_cast<uint4 *>(p.out + plane * p.P + u.node_begin + 8u * w) = val;
+    }
+    flag_error(p.err, err);
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversions between the ABI field n[3][S] (canonical, replica order)
+// and the pre-streamed device form.  One thread per node.
+// ---------------------------------------------------------------------------
+__global__ void k_to_device_form(const uint16_t *__restrict__ n, uint64_t S, uint16_t *__restrict__ B,
+                                 uint64_t P, const uint64_t *__restrict__ abi_off,
+                                 const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
+                                 const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                                 const uint32_t *__restrict__ rep_id, int stream)
+{
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nodes_padded) return;
+    const uint32_t k = chunk_rep[i / 8u];
+    const uint32_t L = rep_L[k];
+    const uint64_t y = i - rep_off[k];
+    if (y >= L) {
+        B[i] = 0; B[P + i] = 0; B[2 * P + i] = 0;
+        return;
+    }
+    const uint64_t a0 = abi_off[rep_id[k]];
+    // B_-1(y) = n_-1(y - 1), B_0(y) = n_0(y), B_+1(y) = n_+1(y + 1)
+    const uint64_t ym = stream ? (y == 0 ? L - 1 : y - 1) : y;
+    const uint64_t yp = stream ? (y + 1 == L ? 0 : y + 1) : y;
+    B[i] = n[a0 + ym];
+    B[P + i] = n[S + a0 + y];
+    B[2 * P + i] = n[2 * S + a0 + yp];
+}
+
+__global__ void k_from_device_form(const uint16_t *__restrict__ B, uint64_t P, uint16_t *__restrict__ n,
+                                   uint64_t S, const uint64_t *__restrict__ abi_off,
+                                   const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
+                                   const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                                   const uint32_t *__restrict__ rep_id, int stream)
+{
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nodes_padded) return;
+    const uint32_t k = chunk_rep[i / 8u];
+    const uint32_t L = rep_L[k];
+    const uint64_t x = i - rep_off[k];
+    if (x >= L) return;
+    const uint64_t base = rep_off[k];
+    const uint64_t a0 = abi_off[rep_id[k]];
+    const uint64_t xr = stream ? (x + 1 == L ? 0 : x + 1) : x;
+    const uint64_t xl = stream ? (x == 0 ? L - 1 : x - 1) : x;
+    n[a0 + x] = B[base + xr];
+    n[S + a0 + x] = B[P + base + x];
+    n[2 * S + a0 + x] = B[2 * P + base + xl];
+}
+
+// Node moments N = a + b + c, J = c - a of the canonical field, in ABI order,
+// and exact int64 totals (block partial sums, then one 64-bit atomic each).
+__global__ void k_moments(const uint16_t *__restrict__ B, uint64_t P, int32_t *__restrict__ N,
+                          int32_t *__restrict__ J, const uint64_t *__restrict__ abi_off,
+                          const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
+                          const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                          const uint32_t *__restrict__ rep_id, int stream,
+                          unsigned long long *__restrict__ totals)
+{
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    long long sn = 0, sj = 0;
+    if (i < nodes_padded) {
+        const uint32_t k = chunk_rep[i / 8u];
+        const uint32_t L = rep_L[k];
+        const uint64_t base = rep_off[k];
+        const uint64_t x = i - base;
+        if (x < L) {
+            const uint64_t xr = stream ? (x + 1 == L ? 0 : x + 1) : x;
+            const uint64_t xl = stream ? (x == 0 ? L - 1 : x - 1) : x;
+            const int32_t a = B[base + xr], b = B[P + base + x], c = B[2 * P + base + xl];
+            const uint64_t o = abi_off[rep_id[k]] + x;
+            if (N) N[o] = a + b + c;
+            if (J) J[o] = c - a;
+            sn = a + b + c;
+            sj = c - a;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        sn += __shfl_down_sync(0xFFFFFFFFu, sn, d);
+        sj += __shfl_down_sync(0xFFFFFFFFu, sj, d);
+    }
+    __shared__ long long ws[2][32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { ws[0][w] = sn; ws[1][w] = sj; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tn = 0, tj = 0;
+        for (int k = 0; k < int(blockDim.x >> 5); ++k) { tn += ws[0][k]; tj += ws[1][k]; }
+        atomicAdd(&totals[0], (unsigned long long)tn);
+        atomicAdd(&totals[1], (unsigned long long)tj);
+    }
+}
+
+// Ensemble statistics of the canonical field, per replica-local position x,
+// pooled over R equal-length replicas (contiguous, offset stride `stride`).
+// Block: 32 positions x (blockDim / 32) replica groups; int64 partial sums
+// are reduced in shared memory and added by one thread per position.  The
+// FP32 path merges the step's batch (R samples) into running means and
+// co-moments with compensated (Kahan) accumulation.
+__global__ void k_stats(const uint16_t *__restrict__ B, uint64_t P, uint32_t L, uint32_t R,
+                        uint64_t stride, int stream, StatsBuffers st)
+{
+    constexpr int kQ = 18;  // 3 sums + 6 products + 9 neighbour products
+    const uint32_t xl = threadIdx.x & 31u, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
+    const uint32_t x = blockIdx.x * 32u + xl;
+    long long acc[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) acc[q] = 0;
+    if (x < L) {
+        const uint32_t x1 = x + 1u == L ? 0u : x + 1u;            // neighbour position
+        const uint32_t xr = stream ? (x + 1u == L ? 0u : x + 1u) : x;
+        const uint32_t xlft = stream ? (x == 0u ? L - 1u : x - 1u) : x;
+        const uint32_t x1r = stream ? (x1 + 1u == L ? 0u : x1 + 1u) : x1;
+        const uint32_t x1l = stream ? (x1 == 0u ? L - 1u : x1 - 1u) : x1;
+        for (uint32_t r = grp; r < R; r += ngrp) {
+            const uint64_t base = r * stride;
+            const long long v0 = B[base + xr], v1 = B[P + base + x], v2 = B[2 * P + base + xlft];
+            const long long w0 = B[base + x1r], w1 = B[P + base + x1], w2 = B[2 * P + base + x1l];
+            acc[0] += v0; acc[1] += v1; acc[2] += v2;
+            acc[3] += v0 * v0; acc[4] += v0 * v1; acc[5] += v0 * v2;
+            acc[6] += v1 * v1; acc[7] += v1 * v2; acc[8] += v2 * v2;
+            acc[9] += v0 * w0; acc[10] += v0 * w1; acc[11] += v0 * w2;
+            acc[12] += v1 * w0; acc[13] += v1 * w1; acc[14] += v1 * w2;
+            acc[15] += v2 * w0; acc[16] += v2 * w1; acc[17] += v2 * w2;
+        }
+    }
+    extern __shared__ long long red[];  // [ngrp][32][kQ]
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) red[(grp * 32u + xl) * kQ + q] = acc[q];
+    __syncthreads();
+    if (grp != 0 || x >= L) return;
+    for (uint32_t g2 = 1; g2 < ngrp; ++g2)
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) acc[q] += red[(g2 * 32u + xl) * kQ + q];
+    for (int q = 0; q < 3; ++q) st.s1[3u * x + q] += acc[q];
+    for (int q = 0; q < 6; ++q) st.s2[6u * x + q] += acc[3 + q];
+    for (int q = 0; q < 9; ++q) st.snb[9u * x + q] += acc[9 + q];
+
+    // FP32 path: batch of R samples at this position.  The batch mean and
+    // co-moment come from the exact integer sums (one rounding each); the
+    // running values are merged with the pairwise update of Chan et al.
+    const float Rb = float(R);
+    const float Ma = float(*st.count);  // samples per position before this batch
+    const float Mt = Ma + Rb;
+    float mb[3];
+    for (int i = 0; i < 3; ++i) mb[i] = float(acc[i]) / Rb;
+    float delta[3];
+    for (int i = 0; i < 3; ++i) {
+        const float m = st.mean32[3u * x + i];
+        delta[i] = mb[i] - m;
+        // compensated m += delta * Rb / Mt
+        const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * x + i];
+        const float nm = m + inc;
+        st.mean32c[3u * x + i] = (nm - m) - inc;
+        st.mean32[3u * x + i] = nm;
+    }
+    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q) {
+        const int i = pi[q], j = pj[q];
+        // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (R s_ij - s_i s_j) / R, exact numerator
+        const long long num = (long long)R * acc[3 + q] - acc[i] * acc[j];
+        const float cb = float(num) / Rb;
+        const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * x + q];
+        const float m2 = st.m2[6u * x + q];
+        const float nm2 = m2 + inc;
+        st.m2c[6u * x + q] = (nm2 - m2) - inc;
+        st.m2[6u * x + q] = nm2;
+    }
+}
+
+__global__ void k_count_add(unsigned long long *count, uint32_t R) { *count += R; }
+
+__global__ void k_philox(const uint4 *__restrict__ ctr, uint64_t n, uint32_t k0, uint32_t k1,
+                         uint4 *__restrict__ out)
+{
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint4 c = ctr[i];
+    philox4x32_10(c.x, c.y, c.z, c.w, k0, k1);
+    out[i] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s)
+{
+    const uint64_t chunks = p.g_end - p.g_begin;
+    if (chunks == 0) return cudaSuccess;
+    const dim3 grid(uint32_t((chunks + kPlainThreads - 1) / kPlainThreads));
+    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
+#define MCLG_PLAIN(O, S, L1) k_step_plain<O, S, L1><<<grid, kPlainThreads, 0, s>>>(p)
+    if (one) {
+        if (stream) { if (l1) MCLG_PLAIN(true, true, true); else MCLG_PLAIN(true, true, false); }
+        else { if (l1) MCLG_PLAIN(true, false, true); else MCLG_PLAIN(true, false, false); }
+    } else {
+        if (stream) { if (l1) MCLG_PLAIN(false, true, true); else MCLG_PLAIN(false, true, false); }
+        else { if (l1) MCLG_PLAIN(false, false, true); else MCLG_PLAIN(false, false, false); }
+    }
+#undef MCLG_PLAIN
+    return cudaGetLastError();
+}
+
+size_t persistent_smem_bytes(uint32_t cap) { return 2u * 3u * size_t(cap) * sizeof(uint16_t); }
+
+cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
+                              bool stream, cudaStream_t s)
+{
+    if (n_units == 0) return cudaSuccess;
+    const size_t smem = persistent_smem_bytes(p.cap);
+    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
+    cudaError_t e = cudaSuccess;
+#define MCLG_PERS(S, L1)                                                                        \
+    do {                                                                                        \
+        e = cudaFuncSetAttribute(k_step_persistent<S, L1>,                                      \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));       \
+        if (e != cudaSuccess) return e;                                                         \
+        k_step_persistent<S, L1><<<n_units, threads, smem, s>>>(p);                             \
+    } while (0)
+    if (stream) { if (l1) MCLG_PERS(true, true); else MCLG_PERS(true, false); }
+    else { if (l1) MCLG_PERS(false, true); else MCLG_PERS(false, false); }
+#undef MCLG_PERS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,
+                                  int stream, cudaStream_t s)
+{
+    const uint64_t np = lay.P;
+    const uint32_t th = 256;
+    k_to_device_form<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
+        n, S, B, lay.P, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+        lay.d_rep_id, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,
+                                    int stream, cudaStream_t s)
+{
+    const uint64_t np = lay.P;
+    const uint32_t th = 256;
+    k_from_device_form<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
+        B, lay.P, n, S, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+        lay.d_rep_id, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
+                           unsigned long long *totals, cudaStream_t s)
+{
+    const uint64_t np = lay.P;
+    const uint32_t th = 256;
+    k_moments<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
+        B, lay.P, N, J, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+        lay.d_rep_id, stream, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
+                         int stream, const StatsBuffers &st, cudaStream_t s)
+{
+    const uint32_t th = 256;
+    const size_t smem = size_t(th) * 18 * sizeof(long long);
+    k_stats<<<(L + 31) / 32, th, smem, s>>>(B, P, L, R, stride, stream, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_count_add<<<1, 1, 0, s>>>(st.count, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint32_t *out,
+                          cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t th = 256;
+    k_philox<<<uint32_t((n + th - 1) / th), th, 0, s>>>(reinterpret_cast<const uint4 *>(ctr), n, k0,
+                                                          k1, reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace mclg

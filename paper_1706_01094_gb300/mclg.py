@@ -1,0 +1,234 @@
+"""Python binding of the C ABI in ``include/mclg.h`` (argument marshalling only).
+
+Every step of the lattice-gas path runs in the sm_103a library
+``_build/libmclg.so``; this module loads it with ctypes and converts numpy
+arrays or torch tensors to pointers.  If the library has not been built, every
+call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MCLG_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
+          4: "occupation overflow", 5: "device wait timed out", 6: "no state set",
+          7: "sampler refinement cap reached"}
+NO_STREAM = 1
+STATS = 2
+MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
+
+EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
+           "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
+           "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox"]
+
+
+class MCLGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, 'unknown')} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_uint32), ("lambda_num", ctypes.c_uint32),
+                ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("mode", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load the built library; raises if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmclg.so is not built ({path}); run "
+                               "paper_1706_01094_gb300.build.build() first")
+        lib = ctypes.CDLL(path)
+        P, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        st = ctypes.c_int
+        lib.mclg_default_params.argtypes = [ctypes.POINTER(Params)]
+        lib.mclg_create.argtypes = [P, u32, u64, ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+        lib.mclg_create.restype = st
+        lib.mclg_init.argtypes = [P, P, P]
+        lib.mclg_init.restype = st
+        lib.mclg_set_state.argtypes = [P, P, u64]
+        lib.mclg_set_state.restype = st
+        lib.mclg_get_state.argtypes = [P, P, ctypes.POINTER(u64)]
+        lib.mclg_get_state.restype = st
+        lib.mclg_step.argtypes = [P, u64]
+        lib.mclg_step.restype = st
+        lib.mclg_moments.argtypes = [P, P, P, P]
+        lib.mclg_moments.restype = st
+        lib.mclg_stats_reset.argtypes = [P]
+        lib.mclg_stats_reset.restype = st
+        lib.mclg_stats_read.argtypes = [P, P, P, P, P, P, P]
+        lib.mclg_stats_read.restype = st
+        lib.mclg_sync.argtypes = [P]
+        lib.mclg_sync.restype = st
+        lib.mclg_time.argtypes = [P]
+        lib.mclg_time.restype = u64
+        lib.mclg_destroy.argtypes = [P]
+        lib.mclg_destroy.restype = None
+        lib.mclg_status_str.argtypes = [st]
+        lib.mclg_status_str.restype = ctypes.c_char_p
+        lib.mclg_philox.argtypes = [P, u64, u64, P, P]
+        lib.mclg_philox.restype = st
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != MCLG_OK:
+        raise MCLGError(status, where)
+
+
+def _ptr(a):
+    """Pointer of a contiguous numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Lattice:
+    """A handle: `replicas` independent periodic D1Q3 lattices of lengths L."""
+
+    def __init__(self, L, seed: int = 1, C: int = 10, lam=(1, 1), flags: int = 0,
+                 mode: int = MODE_AUTO, stream=None):
+        self._lib = load()
+        self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
+        self.S = int(self.L.sum())
+        self.seed = int(seed)
+        p = Params(C, lam[0], lam[1], flags, mode)
+        h = ctypes.c_void_p()
+        _check(self._lib.mclg_create(_ptr(self.L), self.L.size, self.seed & (2**64 - 1),
+                                     ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),
+               "mclg_create")
+        self._h = h
+        self.flags = flags
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mclg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state ---------------------------------------------------------------
+    def init(self, rho, u):
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(-1))
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        if rho.size != self.S or u.size != self.S:
+            raise ValueError("rho and u need one value per node")
+        _check(self._lib.mclg_init(self._h, _ptr(rho), _ptr(u)), "mclg_init")
+
+    def set_state(self, n, t: int = 0):
+        if isinstance(n, np.ndarray):
+            n = np.ascontiguousarray(n, dtype=np.uint16)
+        if tuple(n.shape) not in ((3, self.S), (3 * self.S,)):
+            raise ValueError("state must be [3, S]")
+        _check(self._lib.mclg_set_state(self._h, _ptr(n), t), "mclg_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((3, self.S), dtype=np.uint16)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.mclg_get_state(self._h, _ptr(out), ctypes.byref(t)), "mclg_get_state")
+        return out, int(t.value)
+
+    def step(self, n_steps: int = 1):
+        _check(self._lib.mclg_step(self._h, n_steps), "mclg_step")
+
+    def sync(self):
+        _check(self._lib.mclg_sync(self._h), "mclg_sync")
+
+    def sync_status(self) -> int:
+        return int(self._lib.mclg_sync(self._h))
+
+    @property
+    def t(self) -> int:
+        return int(self._lib.mclg_time(self._h))
+
+    def moments(self, N=None, J=None):
+        if N is None:
+            N = np.zeros(self.S, dtype=np.int32)
+        if J is None:
+            J = np.zeros(self.S, dtype=np.int32)
+        tot = np.zeros(2, dtype=np.int64)
+        _check(self._lib.mclg_moments(self._h, _ptr(N), _ptr(J), _ptr(tot)), "mclg_moments")
+        return N, J, tot
+
+    def totals(self):
+        tot = np.zeros(2, dtype=np.int64)
+        _check(self._lib.mclg_moments(self._h, None, None, _ptr(tot)), "mclg_moments")
+        return tot
+
+    # -- statistics ------------------------------------------------------------
+    def stats_reset(self):
+        _check(self._lib.mclg_stats_reset(self._h), "mclg_stats_reset")
+
+    def stats_read(self):
+        Lc = int(self.L[0])
+        s1 = np.zeros((Lc, 3), dtype=np.int64)
+        s2 = np.zeros((Lc, 6), dtype=np.int64)
+        snb = np.zeros((Lc, 9), dtype=np.int64)
+        cov32 = np.zeros((Lc, 6), dtype=np.float32)
+        cov64 = np.zeros((Lc, 6), dtype=np.float64)
+        cnt = np.zeros(1, dtype=np.uint64)
+        _check(self._lib.mclg_stats_read(self._h, _ptr(s1), _ptr(s2), _ptr(snb), _ptr(cov32),
+                                         _ptr(cov64), _ptr(cnt)), "mclg_stats_read")
+        return {"s1": s1, "s2": s2, "snb": snb, "cov32": cov32, "cov64": cov64,
+                "count": int(cnt[0])}
+
+
+def philox(ctr, seed: int, out=None, stream=None):
+    """The library's device Philox4x32-10 on device uint32 counters ctr[n, 4]."""
+    lib = load()
+    n = int(ctr.shape[0])
+    if out is None:
+        import torch
+        out = torch.empty_like(ctr)
+    _check(lib.mclg_philox(_ptr(ctr), n, seed & (2**64 - 1), _ptr(out), _stream_ptr(stream)),
+           "mclg_philox")
+    return out
