@@ -143,6 +143,26 @@ void mclg_destroy(mclg_handle h);
 /* Static description of a status code. */
 const char *mclg_status_str(mclg_status s);
 
+/* Allocation-free variant of the totals and node moments of mclg_moments,
+ * for callers that cannot allocate device memory: code whose GPU memory is
+ * owned by another pool (a framework's caching allocator may hold nearly all
+ * of it) and loops that cannot accept the device-wide synchronisation that
+ * cudaMalloc/cudaFree may imply.  The paper has no counterpart; this is a
+ * library convenience.
+ *   n       device array, the canonical field n[3][S] (as mclg_get_state writes it)
+ *   S       nodes, 1 <= S <= 2^26 (67,108,864); larger S returns MCLG_ERR_ARG
+ *   N, J    device int32 arrays of S entries, or NULL
+ *   totals  (sum N, sum J) as two int64, host or device, or NULL; a host
+ *           destination synchronises cuda_stream before returning
+ * Allocates nothing: its only scratch is a fixed 512 KiB device array that
+ * every GPU loading this library holds until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race: order them on one stream. */
+mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int32_t *J,
+                                 int64_t *totals, void *cuda_stream);
+
 /* Philox4x32-10 of the library's device generator on n counters: ctr and out
  * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For
  * checking the generator against an independent implementation. */

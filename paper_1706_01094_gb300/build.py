@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmclg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["mclg_kernels.cu", "mclg_api.cu"]
+SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -25,7 +25,8 @@ MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
 
 EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
            "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
-           "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox"]
+           "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox",
+           "mclg_moments_noalloc"]
 
 
 class MCLGError(RuntimeError):
@@ -88,6 +89,8 @@ def load() -> ctypes.CDLL:
         lib.mclg_status_str.restype = ctypes.c_char_p
         lib.mclg_philox.argtypes = [P, u64, u64, P, P]
         lib.mclg_philox.restype = st
+        lib.mclg_moments_noalloc.argtypes = [P, u64, P, P, P, P]
+        lib.mclg_moments_noalloc.restype = st
         _lib = lib
         return lib
 
@@ -220,6 +223,16 @@ class Lattice:
                                          _ptr(cov64), _ptr(cnt)), "mclg_stats_read")
         return {"s1": s1, "s2": s2, "snb": snb, "cov32": cov32, "cov64": cov64,
                 "count": int(cnt[0])}
+
+
+def moments_noalloc(n, N=None, J=None, totals=None, stream=None) -> int:
+    """mclg_moments_noalloc on a device field n[3, S] (caller-owned buffers).
+
+    For callers that cannot allocate device memory; returns the raw status."""
+    lib = load()
+    S = int(n.shape[-1]) if len(n.shape) == 2 else int(n.shape[0]) // 3
+    return int(lib.mclg_moments_noalloc(_ptr(n), S, _ptr(N), _ptr(J), _ptr(totals),
+                                        _stream_ptr(stream)))
 
 
 def philox(ctr, seed: int, out=None, stream=None):
