@@ -48,6 +48,8 @@ struct mclg_ctx {
     // persistent configuration (autotuned)
     bool tuned = false;
     uint32_t p_threads = 256, p_cap = 0;
+    bool plain_tuned = false;
+    uint32_t plain_vec = 4;           // nodes per thread of the plain kernel (autotuned)
     std::vector<Unit> units;
     Unit *d_units = nullptr;
     // statistics
@@ -136,6 +138,7 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.k0 = uint32_t(h->seed);
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
+    a.vec = h->plain_vec;
     return a;
 }
 
@@ -252,6 +255,43 @@ mclg_status autotune(mclg_ctx *h)
     MCLG_CK(cudaMalloc(&h->d_units, h->units.size() * sizeof(Unit)));
     MCLG_CK(cudaMemcpyAsync(h->d_units, h->units.data(), h->units.size() * sizeof(Unit),
                             cudaMemcpyHostToDevice, h->stream));
+    return MCLG_OK;
+}
+
+// Plain-kernel autotuner: time each vector width on the real input, writing
+// into the buffer the next step overwrites anyway (results do not depend on
+// the width), and keep the fastest.
+mclg_status autotune_plain(mclg_ctx *h, uint32_t mode)
+{
+    h->plain_tuned = true;
+    cudaEvent_t e0, e1;
+    MCLG_CK(cudaEventCreate(&e0));
+    MCLG_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    uint32_t best_vec = h->plain_vec;
+    const uint16_t *in = h->d_B[h->cur];
+    uint16_t *outb = h->d_B[h->cur ^ 1];
+    for (uint32_t v : {2u, 4u, 8u}) {
+        h->plain_vec = v;
+        float ms = 0;
+        for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+            MCLG_CK(cudaEventRecord(e0, h->stream));
+            if (mode == MCLG_MODE_PLAIN)
+                MCLG_CK(plain_per_replica_step(h, in, outb, h->t, h->stream));
+            else
+                MCLG_CK(plain_batch_step(h, in, outb, h->t, 0, h->R, h->stream));
+            MCLG_CK(cudaEventRecord(e1, h->stream));
+            MCLG_CK(cudaEventSynchronize(e1));
+            MCLG_CK(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+            best = ms;
+            best_vec = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->plain_vec = best_vec;
     return MCLG_OK;
 }
 
@@ -601,6 +641,10 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     MCLG_CK(cudaSetDevice(h->device));
     const uint32_t mode = effective_mode(h);
     if (mode == MCLG_MODE_PLAIN || mode == 3u) {
+        if (!h->plain_tuned) {
+            mclg_status st = autotune_plain(h, mode);
+            if (st != MCLG_OK) return st;
+        }
         for (uint64_t s = 0; s < n_steps; ++s) {
             const uint16_t *in = h->d_B[h->cur];
             uint16_t *outb = h->d_B[h->cur ^ 1];
@@ -624,6 +668,11 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     if (!h->tuned) {
         mclg_status s = autotune(h);
         if (s != MCLG_OK) return s;
+    }
+    if (!h->plain_tuned && h->n_small < h->R) {
+        // width for the long replicas stepped beside the persistent kernel
+        h->plain_tuned = true;
+        h->plain_vec = 4;
     }
     const int start = h->cur;
     const int final_buf = int((uint64_t(start) + n_steps) & 1u);

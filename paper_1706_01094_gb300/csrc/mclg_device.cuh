@@ -30,14 +30,9 @@ MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-#ifdef __CUDA_ARCH__
-        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
-#else
         const uint64_t p0 = uint64_t(0xD2511F53u) * x0, p1 = uint64_t(0xCD9E8D57u) * x2;
         const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
         const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
-#endif
         const uint32_t y0 = hi1 ^ x1 ^ k0;
         const uint32_t y2 = hi0 ^ x3 ^ k1;
         x0 = y0;
@@ -99,11 +94,32 @@ static __device__ __noinline__ uint32_t refine_decision(int64_t R1, int64_t R2, 
     return 3u;
 }
 
-// C sequential sub-collisions at one node.  (a, b, c) = (n_-1, n_0, n_+1),
-// all <= 65535 on entry; on return the post-collision state.  Error bits go
-// to err (the node stops at the first error).
+// Exact region of one decision from its 12-bit primary chunk q (64-bit integer
+// thresholds, refinement when the chunk leaves the region open).  Returns 0
+// (down), 1 (up), 2 (nothing) or 3 (refinement cap).
+static __device__ __noinline__ uint32_t exact_decision(uint32_t a, uint32_t b, uint32_t c, uint32_t q,
+                                                       uint32_t lam_n, uint32_t lam_d,
+                                                       const NodeKey &nk, uint32_t &next_ref)
+{
+    const uint64_t N = uint64_t(a) + b + c;
+    const uint64_t D = 8ull * N * N * lam_d;
+    const uint64_t T1 = (uint64_t(a * c) << 4) * lam_n;
+    const uint64_t T2 = T1 + uint64_t(b * (b - 1u)) * lam_n;
+    const uint64_t X = uint64_t(q) * D;
+    const uint64_t S1 = T1 << 12, S2 = T2 << 12;
+    if (X + D <= S1) return 0u;
+    if (X >= S1 && X + D <= S2) return 1u;
+    if (X >= S2) return 2u;
+    return refine_decision(int64_t(S1 - X), int64_t(S2 - X), int64_t(D), nk, next_ref);
+}
+
+// C sequential sub-collisions at one node, exact 64-bit integer arithmetic for
+// every decision.  (a, b, c) = (n_-1, n_0, n_+1), all <= 65535 on entry; on
+// return the post-collision state.  Error bits go to err (the node stops at
+// the first error).  Used near the uint16 limit, where every transition must
+// be checked.
 template <bool kLambdaOne>
-__device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t &c,
+__device__ __noinline__ void collide_node_checked(uint32_t &a, uint32_t &b, uint32_t &c,
                                              const NodeKey &nk, uint32_t C, uint32_t lam_n,
                                              uint32_t lam_d, uint32_t &err)
 {
@@ -169,6 +185,106 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
             }
         }
     }
+}
+
+// 1 + q/4096 for a 12-bit chunk already placed at bits [11, 23) (exact).
+__device__ __forceinline__ float unit_of_chunk(uint32_t bits_11_23)
+{
+    return __uint_as_float(0x3F800000u | bits_11_23);
+}
+
+// Chunk m (bits [12m, 12m+12)) of the block, placed at bits [11, 23).
+template <int m>
+__device__ __forceinline__ uint32_t chunk12_at11(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3)
+{
+    constexpr int off = 12 * m, word = off / 32, sh = off % 32;
+    const uint32_t w[4] = {w0, w1, w2, w3};
+    uint32_t v;
+    if constexpr (sh + 12 <= 32) {
+        v = sh >= 11 ? (w[word] >> (sh - 11)) : (w[word] << (11 - sh));
+    } else {
+        v = __funnelshift_r(w[word], w[word + 1], sh - 11);
+    }
+    return v & 0x007FF800u;
+}
+
+// C sequential sub-collisions at one node (Sec. III; D1Q3 table of
+// Sec. III.A), same results as collide_node_checked.
+//
+// Fast path: U's 12-bit prefix gives 1 + q/4096 <= 1 + U < 1 + (q+1)/4096,
+// compared in FP32 with t1 ~ 1 + T1/D and t2 ~ 1 + T2/D.  Their FP32 error
+// is below 5 * 2^-24 (three roundings in K1 = 2 lam / (N^2 lam_d), one in a*c
+// or b*(b-1), one in each fused multiply-add), so a comparison with the
+// margin delta = 2^-20 decides exactly what the integer comparison decides;
+// only when a threshold lies within the margin of the chunk's interval does
+// the decision go to the exact 64-bit path (probability ~2^-11).  States are
+// FP32 integers (exact below 2^24; N <= 3 * 65535).  A node within 2C of the
+// uint16 limit takes collide_node_checked instead.
+template <bool kLambdaOne>
+__device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t &c,
+                                             const NodeKey &nk, uint32_t C, uint32_t lam_n,
+                                             uint32_t lam_d, uint32_t &err)
+{
+    const uint32_t N = a + b + c;
+    if (N < 2u) return;
+    if (max(a, max(b, c)) + 2u * C > 65535u) {
+        collide_node_checked<kLambdaOne>(a, b, c, nk, C, lam_n, lam_d, err);
+        return;
+    }
+    const float fN = float(N);
+    const float K1 = kLambdaOne ? 2.0f / (fN * fN) : float(2u * lam_n) / ((fN * fN) * float(lam_d));
+    const float K2 = K1 * 0.0625f;
+    constexpr float kDelta = 9.5367431640625e-07f;              // 2^-20
+    constexpr float kHi = 2.44140625e-04f + 9.5367431640625e-07f;  // 2^-12 + 2^-20
+    float af = float(a), bf = float(b), cf = float(c);
+    uint32_t next_ref = 0;
+    bool failed = false;
+    for (uint32_t blk = 0; blk * kChunksPerBlock < C; ++blk) {
+        uint32_t w0 = nk.x, w1 = nk.r, w2 = nk.t, w3 = (kPurposeCollide << 28) | blk;
+        philox4x32_10(w0, w1, w2, w3, nk.k0, nk.k1);
+        const uint32_t base = blk * kChunksPerBlock;
+        uint32_t qb[kChunksPerBlock];
+        qb[0] = chunk12_at11<0>(w0, w1, w2, w3);
+        qb[1] = chunk12_at11<1>(w0, w1, w2, w3);
+        qb[2] = chunk12_at11<2>(w0, w1, w2, w3);
+        qb[3] = chunk12_at11<3>(w0, w1, w2, w3);
+        qb[4] = chunk12_at11<4>(w0, w1, w2, w3);
+        qb[5] = chunk12_at11<5>(w0, w1, w2, w3);
+        qb[6] = chunk12_at11<6>(w0, w1, w2, w3);
+        qb[7] = chunk12_at11<7>(w0, w1, w2, w3);
+        qb[8] = chunk12_at11<8>(w0, w1, w2, w3);
+        qb[9] = chunk12_at11<9>(w0, w1, w2, w3);
+#pragma unroll
+        for (int m = 0; m < kChunksPerBlock; ++m) {
+            if (base + m >= C) break;
+            const float uq = unit_of_chunk(qb[m]);
+            const float lo = uq - kDelta;   // below 1 + U by more than the error
+            const float hi = uq + kHi;      // above 1 + U by more than the error
+            const float t1 = fmaf(af * cf, K1, 1.0f);
+            const float t2 = fmaf(bf * (bf - 1.0f), K2, t1);
+            const bool down = hi <= t1;
+            const bool up = lo >= t1 && hi <= t2;
+            const bool none = lo >= t2;
+            float s = down ? -1.0f : (up ? 1.0f : 0.0f);
+            if (!(down || up || none)) {
+                const uint32_t region = exact_decision(uint32_t(af), uint32_t(bf), uint32_t(cf),
+                                                       qb[m] >> 11, lam_n, lam_d, nk, next_ref);
+                failed |= region == 3u;
+                s = region == 0u ? -1.0f : (region == 1u ? 1.0f : 0.0f);
+            }
+            af += s;
+            cf += s;
+            bf = fmaf(-2.0f, s, bf);
+        }
+    }
+    if (failed) {
+        // a decision hit the refinement cap: report it like the checked path
+        // (the state after an error is unspecified)
+        err |= kErrSampler;
+    }
+    a = uint32_t(af);
+    b = uint32_t(bf);
+    c = uint32_t(cf);
 }
 
 }  // namespace mclg

@@ -34,6 +34,7 @@ struct PlainArgs {
     uint32_t one_L, one_rid;
     uint32_t t, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
+    uint32_t vec;  // nodes per thread: 2, 4 or 8
 };
 
 struct Unit {

@@ -23,18 +23,31 @@ namespace mclg {
 __device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
 __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 
-__device__ __forceinline__ void unpack8(const uint4 v, uint32_t e[8])
-{
-    e[0] = lo16(v.x); e[1] = hi16(v.x);
-    e[2] = lo16(v.y); e[3] = hi16(v.y);
-    e[4] = lo16(v.z); e[5] = hi16(v.z);
-    e[6] = lo16(v.w); e[7] = hi16(v.w);
-}
+// V consecutive uint16 values per thread: one 4-, 8- or 16-byte vector.
+template <int V> struct VecT;
+template <> struct VecT<2> { using T = uint32_t; };
+template <> struct VecT<4> { using T = uint2; };
+template <> struct VecT<8> { using T = uint4; };
 
-__device__ __forceinline__ uint4 pack8(const uint32_t e[8])
+__device__ __forceinline__ void unpack(uint32_t v, uint32_t e[2]) { e[0] = lo16(v); e[1] = hi16(v); }
+__device__ __forceinline__ void unpack(uint2 v, uint32_t e[4])
 {
-    return make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
-                      e[6] | (e[7] << 16));
+    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
+}
+__device__ __forceinline__ void unpack(uint4 v, uint32_t e[8])
+{
+    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
+    e[4] = lo16(v.z); e[5] = hi16(v.z); e[6] = lo16(v.w); e[7] = hi16(v.w);
+}
+__device__ __forceinline__ void pack(const uint32_t e[2], uint32_t &v) { v = e[0] | (e[1] << 16); }
+__device__ __forceinline__ void pack(const uint32_t e[4], uint2 &v)
+{
+    v = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+}
+__device__ __forceinline__ void pack(const uint32_t e[8], uint4 &v)
+{
+    v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                   e[6] | (e[7] << 16));
 }
 
 __device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
@@ -43,17 +56,21 @@ __device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
 }
 
 // ---------------------------------------------------------------------------
-// Plain kernel: one thread per 8-node chunk, any set of whole replicas laid
-// out contiguously (chunk range [g_begin, g_end)).  kOne: a single replica
-// whose offset, length and id come from the arguments (no table reads).
+// Plain kernel: one thread per V consecutive nodes, any set of whole replicas
+// laid out contiguously (node range [8 g_begin, 8 g_end)).  kOne: a single
+// replica whose offset, length and id come from the arguments (no tables).
 // ---------------------------------------------------------------------------
-template <bool kOne, bool kStream, bool kLambdaOne>
+template <int V, bool kOne, bool kStream, bool kLambdaOne>
 __global__ void __launch_bounds__(kPlainThreads)
     k_step_plain(PlainArgs p)
 {
+    using T = typename VecT<V>::T;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t g = p.g_begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const bool active = g < p.g_end;
+    const uint64_t v_begin = p.g_begin * (8 / V), v_end = p.g_end * (8 / V);
+    const uint64_t g = v_begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool active = g < v_end;
+    const uint64_t gv = active ? g : v_end - 1;  // idle lanes mirror the last vector
+    const uint64_t node0 = gv * V;
 
     uint64_t off;
     uint32_t L, rid;
@@ -62,45 +79,40 @@ __global__ void __launch_bounds__(kPlainThreads)
         L = p.one_L;
         rid = p.one_rid;
     } else {
-        const uint32_t k = active ? p.chunk_rep[g] : p.chunk_rep[p.g_end - 1];
+        const uint32_t k = p.chunk_rep[node0 / 8u];
         off = p.rep_off[k];
         L = p.rep_L[k];
         rid = p.rep_id[k];
     }
-    const uint64_t node0 = (active ? g : p.g_end - 1) * 8u;  // first node of the chunk
-    const uint32_t x0 = uint32_t(node0 - off);                 // replica-local
+    const uint32_t x0 = uint32_t(node0 - off);  // replica-local
 
     const uint16_t *__restrict__ inm = p.in;
     const uint16_t *__restrict__ in0 = p.in + p.P;
     const uint16_t *__restrict__ inp = p.in + 2 * p.P;
 
-    const uint4 vm = __ldcs(reinterpret_cast<const uint4 *>(inm + node0));
-    const uint4 v0 = __ldcs(reinterpret_cast<const uint4 *>(in0 + node0));
-    const uint4 vp = __ldcs(reinterpret_cast<const uint4 *>(inp + node0));
+    uint32_t em[V], e0[V], ep[V];
+    unpack(__ldcs(reinterpret_cast<const T *>(inm + node0)), em);
+    unpack(__ldcs(reinterpret_cast<const T *>(in0 + node0)), e0);
+    unpack(__ldcs(reinterpret_cast<const T *>(inp + node0)), ep);
 
-    uint32_t em[8], e0[8], ep[8];
-    unpack8(vm, em);
-    unpack8(v0, e0);
-    unpack8(vp, ep);
-
-    // Halo: the v = -1 value right of the chunk and the v = +1 value left of it.
+    // Halo: the v = -1 value right of the vector and the v = +1 value left of it.
     uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
-    uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[7], 1);
+    uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
     if (kStream) {
-        if (!(lane < 31u && x0 + 8u < L)) nxt = inm[off + (x0 + 8u < L ? x0 + 8u : 0u)];
+        if (!(lane < 31u && x0 + V < L)) nxt = inm[off + (x0 + V < L ? x0 + V : 0u)];
         if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
     }
-    const uint32_t e = L - x0 < 8u ? L - x0 : 8u;  // valid nodes in this chunk
+    const uint32_t e = L - x0 < uint32_t(V) ? L - x0 : uint32_t(V);  // valid nodes here
 
     uint32_t err = 0;
-    uint32_t om[8], o0[8], op[8];
+    uint32_t om[V], o0[V], op[V];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < V; ++j) {
         uint32_t a, b, c;
         if (kStream) {
-            a = (uint32_t(j) + 1u < e) ? em[(j + 1) & 7] : nxt;
+            a = (uint32_t(j) + 1u < e) ? em[(j + 1) % V] : nxt;
             b = e0[j];
-            c = (j > 0) ? ep[(j + 7) & 7] : prv;
+            c = (j > 0) ? ep[(j + V - 1) % V] : prv;
         } else {
             a = em[j];
             b = e0[j];
@@ -117,9 +129,13 @@ __global__ void __launch_bounds__(kPlainThreads)
         op[j] = c;
     }
     if (active) {
-        __stcs(reinterpret_cast<uint4 *>(p.out + node0), pack8(om));
-        __stcs(reinterpret_cast<uint4 *>(p.out + p.P + node0), pack8(o0));
-        __stcs(reinterpret_cast<uint4 *>(p.out + 2 * p.P + node0), pack8(op));
+        T vo;
+        pack(om, vo);
+        __stcs(reinterpret_cast<T *>(p.out + node0), vo);
+        pack(o0, vo);
+        __stcs(reinterpret_cast<T *>(p.out + p.P + node0), vo);
+        pack(op, vo);
+        __stcs(reinterpret_cast<T *>(p.out + 2 * p.P + node0), vo);
         flag_error(p.err, err);
     }
 }
@@ -385,13 +401,11 @@ __global__ void k_philox(const uint4 *__restrict__ ctr, uint64_t n, uint32_t k0,
 // ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
-cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s)
+template <int V>
+static void launch_plain_v(const PlainArgs &p, bool one, bool stream, bool l1, dim3 grid,
+                           cudaStream_t s)
 {
-    const uint64_t chunks = p.g_end - p.g_begin;
-    if (chunks == 0) return cudaSuccess;
-    const dim3 grid(uint32_t((chunks + kPlainThreads - 1) / kPlainThreads));
-    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
-#define MCLG_PLAIN(O, S, L1) k_step_plain<O, S, L1><<<grid, kPlainThreads, 0, s>>>(p)
+#define MCLG_PLAIN(O, S, L1) k_step_plain<V, O, S, L1><<<grid, kPlainThreads, 0, s>>>(p)
     if (one) {
         if (stream) { if (l1) MCLG_PLAIN(true, true, true); else MCLG_PLAIN(true, true, false); }
         else { if (l1) MCLG_PLAIN(true, false, true); else MCLG_PLAIN(true, false, false); }
@@ -400,6 +414,20 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t
         else { if (l1) MCLG_PLAIN(false, false, true); else MCLG_PLAIN(false, false, false); }
     }
 #undef MCLG_PLAIN
+}
+
+cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s)
+{
+    const uint64_t chunks = p.g_end - p.g_begin;
+    if (chunks == 0) return cudaSuccess;
+    const uint32_t V = p.vec;
+    const uint64_t threads = chunks * (8u / V);
+    const dim3 grid(uint32_t((threads + kPlainThreads - 1) / kPlainThreads));
+    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
+    if (V == 2) launch_plain_v<2>(p, one, stream, l1, grid, s);
+    else if (V == 4) launch_plain_v<4>(p, one, stream, l1, grid, s);
+    else if (V == 8) launch_plain_v<8>(p, one, stream, l1, grid, s);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
