@@ -274,6 +274,7 @@ def run_gb300(args):
     lat.sync()
     torch.cuda.synchronize()
     barrier()
+    tuning = lat.tuning()
     ms = ev0.elapsed_time(ev1)
     t_max = ms
     if world > 1:
@@ -329,7 +330,7 @@ def run_gb300(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic: Poisson(f^eq) initial state of the paper-shaped workload",
-            "config": config_dict(wl, args, world),
+            "config": {**config_dict(wl, args, world), "tuning": tuning},
             "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
                          "unit": "Gop/s", "frac": achieved_ops / alu_peak,
                          "traffic": traffic, "kernel": kernel,

@@ -137,6 +137,13 @@ mclg_status mclg_sync(mclg_handle h);
 /* Current time step of the handle (host-side counter, no synchronisation). */
 uint64_t mclg_time(mclg_handle h);
 
+/* The autotuned launch configuration of the handle (zeros before the first
+ * mclg_step): cfg[0] = 100 * nodes per thread of the plain kernel + its
+ * variant index (register bound), cfg[1] = threads
+ * per persistent CTA, cfg[2] = nodes per persistent work unit, cfg[3] = number
+ * of persistent work units. */
+mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[4]);
+
 /* Release every resource of the handle.  NULL-safe. */
 void mclg_destroy(mclg_handle h);
 

@@ -49,7 +49,7 @@ struct mclg_ctx {
     bool tuned = false;
     uint32_t p_threads = 256, p_cap = 0;
     bool plain_tuned = false;
-    uint32_t plain_vec = 4;           // nodes per thread of the plain kernel (autotuned)
+    uint32_t plain_variant = 0;       // plain-kernel variant (autotuned)
     std::vector<Unit> units;
     Unit *d_units = nullptr;
     // statistics
@@ -138,7 +138,8 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.k0 = uint32_t(h->seed);
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
-    a.vec = h->plain_vec;
+    a.variant = h->plain_variant;
+    a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
     return a;
 }
 
@@ -156,9 +157,9 @@ cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uin
         a.one_off = h->rep_off[k_begin];
         a.one_L = h->rep_L[k_begin];
         a.one_rid = h->order[k_begin];
-        return launch_plain(a, true, streaming(h), s);
+        return launch_plain(a, true, s);
     }
-    return launch_plain(a, false, streaming(h), s);
+    return launch_plain(a, false, s);
 }
 
 // One step with one plain launch per replica (the per-replica baseline).
@@ -192,6 +193,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.k0 = uint32_t(h->seed);
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
+    a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
     return a;
 }
 
@@ -226,9 +228,9 @@ mclg_status autotune(mclg_ctx *h)
             PersistentArgs a = persistent_args(h, h->d_B[h->cur], scratch, h->t, probe_steps,
                                                d_units, cap);
             // warm-up, then timed
-            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, streaming(h), h->stream));
+            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, h->stream));
             MCLG_CK(cudaEventRecord(e0, h->stream));
-            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, streaming(h), h->stream));
+            MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, h->stream));
             MCLG_CK(cudaEventRecord(e1, h->stream));
             MCLG_CK(cudaEventSynchronize(e1));
             float ms = 0;
@@ -268,11 +270,11 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode)
     MCLG_CK(cudaEventCreate(&e0));
     MCLG_CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    uint32_t best_vec = h->plain_vec;
+    uint32_t best_variant = h->plain_variant;
     const uint16_t *in = h->d_B[h->cur];
     uint16_t *outb = h->d_B[h->cur ^ 1];
-    for (uint32_t v : {2u, 4u, 8u}) {
-        h->plain_vec = v;
+    for (uint32_t v = 0; v < kPlainVariants; ++v) {
+        h->plain_variant = v;
         float ms = 0;
         for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
             MCLG_CK(cudaEventRecord(e0, h->stream));
@@ -286,12 +288,12 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode)
         }
         if (ms < best) {
             best = ms;
-            best_vec = v;
+            best_variant = v;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->plain_vec = best_vec;
+    h->plain_variant = best_variant;
     return MCLG_OK;
 }
 
@@ -672,7 +674,7 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     if (!h->plain_tuned && h->n_small < h->R) {
         // width for the long replicas stepped beside the persistent kernel
         h->plain_tuned = true;
-        h->plain_vec = 4;
+        h->plain_variant = 0;
     }
     const int start = h->cur;
     const int final_buf = int((uint64_t(start) + n_steps) & 1u);
@@ -694,7 +696,7 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     while (done < n_steps) {
         const uint32_t chunk = uint32_t(std::min<uint64_t>(n_steps - done, 65536u));
         PersistentArgs a = persistent_args(h, in, outb, h->t + done, chunk, h->d_units, h->p_cap);
-        MCLG_CK(launch_persistent(a, uint32_t(h->units.size()), h->p_threads, streaming(h), h->stream));
+        MCLG_CK(launch_persistent(a, uint32_t(h->units.size()), h->p_threads, h->stream));
         in = outb;
         done += chunk;
     }
@@ -797,6 +799,16 @@ mclg_status mclg_sync(mclg_handle h)
 }
 
 uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
+
+mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[4])
+{
+    if (!h || !cfg) return MCLG_ERR_ARG;
+    cfg[0] = h->plain_tuned ? plain_variant_vec(h->plain_variant) * 100u + h->plain_variant : 0u;
+    cfg[1] = h->tuned ? h->p_threads : 0u;
+    cfg[2] = h->tuned ? h->p_cap : 0u;
+    cfg[3] = h->tuned ? uint32_t(h->units.size()) : 0u;
+    return MCLG_OK;
+}
 
 mclg_status mclg_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out, void *cuda_stream)
 {

@@ -213,14 +213,14 @@ __device__ __forceinline__ uint32_t chunk12_at11(uint32_t w0, uint32_t w1, uint3
 //
 // Fast path: U's 12-bit prefix gives 1 + q/4096 <= 1 + U < 1 + (q+1)/4096,
 // compared in FP32 with t1 ~ 1 + T1/D and t2 ~ 1 + T2/D.  Their FP32 error
-// is below 5 * 2^-24 (three roundings in K1 = 2 lam / (N^2 lam_d), one in a*c
-// or b*(b-1), one in each fused multiply-add), so a comparison with the
-// margin delta = 2^-20 decides exactly what the integer comparison decides;
+// is below 7 * 2^-24 (K1 = 2 lam / (N^2 lam_d): two roundings and a 2-ulp
+// __fdividef; one rounding in a*c or b*(b-1); one in each fused
+// multiply-add), so a comparison with the margin delta = 2^-20 = 16 * 2^-24
+// decides exactly what the integer comparison decides;
 // only when a threshold lies within the margin of the chunk's interval does
 // the decision go to the exact 64-bit path (probability ~2^-11).  States are
 // FP32 integers (exact below 2^24; N <= 3 * 65535).  A node within 2C of the
 // uint16 limit takes collide_node_checked instead.
-template <bool kLambdaOne>
 __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t &c,
                                              const NodeKey &nk, uint32_t C, uint32_t lam_n,
                                              uint32_t lam_d, uint32_t &err)
@@ -228,15 +228,18 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
     const uint32_t N = a + b + c;
     if (N < 2u) return;
     if (max(a, max(b, c)) + 2u * C > 65535u) {
-        collide_node_checked<kLambdaOne>(a, b, c, nk, C, lam_n, lam_d, err);
+        collide_node_checked<false>(a, b, c, nk, C, lam_n, lam_d, err);
         return;
     }
-    const float fN = float(N);
-    const float K1 = kLambdaOne ? 2.0f / (fN * fN) : float(2u * lam_n) / ((fN * fN) * float(lam_d));
+    const float fN = __uint_as_float(N | 0x4B000000u) - 8388608.0f;  // exact, N < 2^23
+    // __fdividef: within 2 ulp, covered by the comparison margin
+    const float K1 = __fdividef(float(2u * lam_n), (fN * fN) * float(lam_d));
     const float K2 = K1 * 0.0625f;
     constexpr float kDelta = 9.5367431640625e-07f;              // 2^-20
     constexpr float kHi = 2.44140625e-04f + 9.5367431640625e-07f;  // 2^-12 + 2^-20
-    float af = float(a), bf = float(b), cf = float(c);
+    float af = __uint_as_float(a | 0x4B000000u) - 8388608.0f;
+    float bf = __uint_as_float(b | 0x4B000000u) - 8388608.0f;
+    float cf = __uint_as_float(c | 0x4B000000u) - 8388608.0f;
     uint32_t next_ref = 0;
     bool failed = false;
     for (uint32_t blk = 0; blk * kChunksPerBlock < C; ++blk) {
@@ -282,9 +285,9 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
         // (the state after an error is unspecified)
         err |= kErrSampler;
     }
-    a = uint32_t(af);
-    b = uint32_t(bf);
-    c = uint32_t(cf);
+    a = __float_as_uint(af + 8388608.0f) & 0x7FFFFFu;
+    b = __float_as_uint(bf + 8388608.0f) & 0x7FFFFFu;
+    c = __float_as_uint(cf + 8388608.0f) & 0x7FFFFFu;
 }
 
 }  // namespace mclg

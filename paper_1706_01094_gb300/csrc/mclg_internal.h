@@ -10,6 +10,7 @@ constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain
 constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CTA size
 constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
 constexpr uint32_t kMaxUnitNodes = 16384;        // shared-memory capacity of a persistent CTA
+constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
 
 // Device-resident description of the internal replica order.
 struct Layout {
@@ -34,7 +35,8 @@ struct PlainArgs {
     uint32_t one_L, one_rid;
     uint32_t t, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
-    uint32_t vec;  // nodes per thread: 2, 4 or 8
+    uint32_t variant;  // plain-kernel variant (nodes per thread, register bound)
+    uint32_t stream;   // 1: pull-stream before colliding, 0: collide only
 };
 
 struct Unit {
@@ -54,6 +56,7 @@ struct PersistentArgs {
     uint32_t cap;  // shared-memory nodes per buffer (>= every unit's nodes)
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
+    uint32_t stream;  // 1: pull-stream before colliding, 0: collide only
 };
 
 struct StatsBuffers {
@@ -63,10 +66,11 @@ struct StatsBuffers {
     unsigned long long *count;  // samples per position
 };
 
-cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s);
+cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
+uint32_t plain_variant_vec(uint32_t variant);
 size_t persistent_smem_bytes(uint32_t cap);
 cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
-                              bool stream, cudaStream_t s);
+                              cudaStream_t s);
 cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,
                                   int stream, cudaStream_t s);
 cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,

@@ -23,12 +23,14 @@ namespace mclg {
 __device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
 __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 
-// V consecutive uint16 values per thread: one 4-, 8- or 16-byte vector.
+// V consecutive uint16 values per thread: one 2-, 4-, 8- or 16-byte vector.
 template <int V> struct VecT;
+template <> struct VecT<1> { using T = uint16_t; };
 template <> struct VecT<2> { using T = uint32_t; };
 template <> struct VecT<4> { using T = uint2; };
 template <> struct VecT<8> { using T = uint4; };
 
+__device__ __forceinline__ void unpack(uint16_t v, uint32_t e[1]) { e[0] = v; }
 __device__ __forceinline__ void unpack(uint32_t v, uint32_t e[2]) { e[0] = lo16(v); e[1] = hi16(v); }
 __device__ __forceinline__ void unpack(uint2 v, uint32_t e[4])
 {
@@ -39,6 +41,7 @@ __device__ __forceinline__ void unpack(uint4 v, uint32_t e[8])
     e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
     e[4] = lo16(v.z); e[5] = hi16(v.z); e[6] = lo16(v.w); e[7] = hi16(v.w);
 }
+__device__ __forceinline__ void pack(const uint32_t e[1], uint16_t &v) { v = uint16_t(e[0]); }
 __device__ __forceinline__ void pack(const uint32_t e[2], uint32_t &v) { v = e[0] | (e[1] << 16); }
 __device__ __forceinline__ void pack(const uint32_t e[4], uint2 &v)
 {
@@ -60,10 +63,11 @@ __device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
 // laid out contiguously (node range [8 g_begin, 8 g_end)).  kOne: a single
 // replica whose offset, length and id come from the arguments (no tables).
 // ---------------------------------------------------------------------------
-template <int V, bool kOne, bool kStream, bool kLambdaOne>
-__global__ void __launch_bounds__(kPlainThreads)
+template <int V, int kMinBlocks, bool kOne>
+__global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
     k_step_plain(PlainArgs p)
 {
+    const bool kStream = p.stream != 0u;
     using T = typename VecT<V>::T;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t v_begin = p.g_begin * (8 / V), v_end = p.g_end * (8 / V);
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(kPlainThreads)
         }
         if (uint32_t(j) < e) {
             const NodeKey nk{x0 + uint32_t(j), rid, p.t, p.k0, p.k1};
-            collide_node<kLambdaOne>(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+            collide_node(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
         } else {
             a = b = c = 0u;
         }
@@ -145,9 +149,9 @@ __global__ void __launch_bounds__(kPlainThreads)
 // `cap` padded nodes), held in shared memory for all n_steps steps.  Two
 // shared buffers alternate; one barrier per step.
 // ---------------------------------------------------------------------------
-template <bool kStream, bool kLambdaOne>
-__global__ void __launch_bounds__(kPersistentMaxThreads) k_step_persistent(PersistentArgs p)
+__global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(PersistentArgs p)
 {
+    const bool kStream = p.stream != 0u;
     extern __shared__ __align__(16) uint16_t smem[];
     __shared__ uint32_t s_lo[kMaxUnitReplicas + 1];  // unit-local replica starts
     __shared__ uint32_t s_L[kMaxUnitReplicas];
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_step_persistent(Persi
                     c = bp[i];
                 }
                 const NodeKey nk{x, s_rid[lo], t, p.k0, p.k1};
-                collide_node<kLambdaOne>(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+                collide_node(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
             }
             om[i] = uint16_t(a);
             o0[i] = uint16_t(b);
@@ -401,55 +405,53 @@ __global__ void k_philox(const uint4 *__restrict__ ctr, uint64_t n, uint32_t k0,
 // ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
-template <int V>
-static void launch_plain_v(const PlainArgs &p, bool one, bool stream, bool l1, dim3 grid,
-                           cudaStream_t s)
+template <int V, int kMinBlocks>
+static void launch_plain_v(const PlainArgs &p, bool one, dim3 grid, cudaStream_t s)
 {
-#define MCLG_PLAIN(O, S, L1) k_step_plain<V, O, S, L1><<<grid, kPlainThreads, 0, s>>>(p)
-    if (one) {
-        if (stream) { if (l1) MCLG_PLAIN(true, true, true); else MCLG_PLAIN(true, true, false); }
-        else { if (l1) MCLG_PLAIN(true, false, true); else MCLG_PLAIN(true, false, false); }
-    } else {
-        if (stream) { if (l1) MCLG_PLAIN(false, true, true); else MCLG_PLAIN(false, true, false); }
-        else { if (l1) MCLG_PLAIN(false, false, true); else MCLG_PLAIN(false, false, false); }
-    }
-#undef MCLG_PLAIN
+    if (one) k_step_plain<V, kMinBlocks, true><<<grid, kPlainThreads, 0, s>>>(p);
+    else k_step_plain<V, kMinBlocks, false><<<grid, kPlainThreads, 0, s>>>(p);
 }
 
-cudaError_t launch_plain(const PlainArgs &p, bool one, bool stream, cudaStream_t s)
+// Plain-kernel variants: (nodes per thread, minimum CTAs per SM).  More
+// nodes per thread give more independent work per thread; a higher CTA bound
+// caps registers for occupancy.  The autotuner picks one per handle.
+static const uint32_t kVariantVec[kPlainVariants] = {1, 1, 1, 2, 2, 4};
+
+uint32_t plain_variant_vec(uint32_t variant)
+{
+    return kVariantVec[variant < kPlainVariants ? variant : 0];
+}
+
+cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s)
 {
     const uint64_t chunks = p.g_end - p.g_begin;
     if (chunks == 0) return cudaSuccess;
-    const uint32_t V = p.vec;
+    if (p.variant >= kPlainVariants) return cudaErrorInvalidValue;
+    const uint32_t V = plain_variant_vec(p.variant);
     const uint64_t threads = chunks * (8u / V);
     const dim3 grid(uint32_t((threads + kPlainThreads - 1) / kPlainThreads));
-    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
-    if (V == 2) launch_plain_v<2>(p, one, stream, l1, grid, s);
-    else if (V == 4) launch_plain_v<4>(p, one, stream, l1, grid, s);
-    else if (V == 8) launch_plain_v<8>(p, one, stream, l1, grid, s);
-    else return cudaErrorInvalidValue;
+    switch (p.variant) {
+    case 0: launch_plain_v<1, 4>(p, one, grid, s); break;
+    case 1: launch_plain_v<1, 6>(p, one, grid, s); break;   // <= 40 registers
+    case 2: launch_plain_v<1, 8>(p, one, grid, s); break;   // <= 32 registers
+    case 3: launch_plain_v<2, 4>(p, one, grid, s); break;   // <= 64 registers
+    case 4: launch_plain_v<2, 1>(p, one, grid, s); break;
+    default: launch_plain_v<4, 1>(p, one, grid, s); break;
+    }
     return cudaGetLastError();
 }
 
 size_t persistent_smem_bytes(uint32_t cap) { return 2u * 3u * size_t(cap) * sizeof(uint16_t); }
 
 cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
-                              bool stream, cudaStream_t s)
+                              cudaStream_t s)
 {
     if (n_units == 0) return cudaSuccess;
     const size_t smem = persistent_smem_bytes(p.cap);
-    const bool l1 = p.lam_n == 1u && p.lam_d == 1u;
-    cudaError_t e = cudaSuccess;
-#define MCLG_PERS(S, L1)                                                                        \
-    do {                                                                                        \
-        e = cudaFuncSetAttribute(k_step_persistent<S, L1>,                                      \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));       \
-        if (e != cudaSuccess) return e;                                                         \
-        k_step_persistent<S, L1><<<n_units, threads, smem, s>>>(p);                             \
-    } while (0)
-    if (stream) { if (l1) MCLG_PERS(true, true); else MCLG_PERS(true, false); }
-    else { if (l1) MCLG_PERS(false, true); else MCLG_PERS(false, false); }
-#undef MCLG_PERS
+    cudaError_t e = cudaFuncSetAttribute(k_step_persistent,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_step_persistent<<<n_units, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
 EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
            "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
            "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox",
-           "mclg_moments_noalloc"]
+           "mclg_moments_noalloc", "mclg_tuning"]
 
 
 class MCLGError(RuntimeError):
@@ -89,6 +89,8 @@ def load() -> ctypes.CDLL:
         lib.mclg_status_str.restype = ctypes.c_char_p
         lib.mclg_philox.argtypes = [P, u64, u64, P, P]
         lib.mclg_philox.restype = st
+        lib.mclg_tuning.argtypes = [P, P]
+        lib.mclg_tuning.restype = st
         lib.mclg_moments_noalloc.argtypes = [P, u64, P, P, P, P]
         lib.mclg_moments_noalloc.restype = st
         _lib = lib
@@ -188,6 +190,12 @@ class Lattice:
 
     def sync_status(self) -> int:
         return int(self._lib.mclg_sync(self._h))
+
+    def tuning(self) -> dict:
+        cfg = np.zeros(4, dtype=np.uint32)
+        _check(self._lib.mclg_tuning(self._h, _ptr(cfg)), "mclg_tuning")
+        return {"plain_nodes_per_thread": int(cfg[0]), "persistent_threads": int(cfg[1]),
+                "persistent_unit_nodes": int(cfg[2]), "persistent_units": int(cfg[3])}
 
     @property
     def t(self) -> int:
