@@ -140,6 +140,7 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.err = h->d_err;
     a.variant = h->plain_variant;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.rk = make_round_keys(h->seed);
     return a;
 }
 
@@ -194,6 +195,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.rk = make_round_keys(h->seed);
     return a;
 }
 

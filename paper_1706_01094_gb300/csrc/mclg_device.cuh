@@ -42,6 +42,41 @@ MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x
     }
 }
 
+// The ten round keys of Philox4x32-10 for one seed, precomputed once per launch
+// (they are the same for every counter).
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+MCLG_HD RoundKeys make_round_keys(uint64_t seed)
+{
+    RoundKeys rk;
+    uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        rk.k0[i] = k0;
+        rk.k1[i] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+// philox4x32_10 with precomputed round keys.
+MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+                           const RoundKeys &rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = uint64_t(0xD2511F53u) * x0, p1 = uint64_t(0xCD9E8D57u) * x2;
+        const uint32_t y0 = uint32_t(p1 >> 32) ^ x1 ^ rk.k0[round];
+        const uint32_t y2 = uint32_t(p0 >> 32) ^ x3 ^ rk.k1[round];
+        x1 = uint32_t(p1);
+        x3 = uint32_t(p0);
+        x0 = y0;
+        x2 = y2;
+    }
+}
+
 // Bits [12m, 12m + 12) of the 128-bit block (w0 least significant), m in 0..9.
 template <int m>
 __device__ __forceinline__ uint32_t chunk12(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3)
@@ -187,11 +222,6 @@ __device__ __noinline__ void collide_node_checked(uint32_t &a, uint32_t &b, uint
     }
 }
 
-// 1 + q/4096 for a 12-bit chunk already placed at bits [11, 23) (exact).
-__device__ __forceinline__ float unit_of_chunk(uint32_t bits_11_23)
-{
-    return __uint_as_float(0x3F800000u | bits_11_23);
-}
 
 // Chunk m (bits [12m, 12m+12)) of the block, placed at bits [11, 23).
 template <int m>
@@ -208,22 +238,68 @@ __device__ __forceinline__ uint32_t chunk12_at11(uint32_t w0, uint32_t w1, uint3
     return v & 0x007FF800u;
 }
 
-// C sequential sub-collisions at one node (Sec. III; D1Q3 table of
-// Sec. III.A), same results as collide_node_checked.
+// One sub-collision of the FP32 fast path (see fast_block); qbits = q << 11.
+__device__ __forceinline__ void fast_sub_collision(float &af, float &bm1, float &cf, float K1,
+                                                   float K2, uint32_t qbits, const NodeKey &nk,
+                                                   uint32_t lam_n, uint32_t lam_d,
+                                                   uint32_t &next_ref, bool &failed)
+{
+    const float lo = __uint_as_float(qbits + 0x3F7FFFF8u);  // 1 + q/4096 - 2^-20
+    const float hi = __uint_as_float(qbits + 0x3F800808u);  // 1 + (q+1)/4096 + 2^-20
+    const float t1 = fmaf(af * cf, K1, 1.0f);
+    const float t2 = fmaf(fmaf(bm1, bm1, bm1), K2, t1);     // b (b - 1) = bm1^2 + bm1
+    const bool down = hi <= t1;
+    const bool up = lo >= t1 && hi <= t2;
+    const bool none = lo >= t2;
+    float s = down ? -1.0f : (up ? 1.0f : 0.0f);
+    if (!(down || up || none)) {
+        const uint32_t a = __float_as_uint(af + 8388608.0f) & 0x7FFFFFu;
+        const uint32_t b = __float_as_uint(bm1 + 8388609.0f) & 0x7FFFFFu;
+        const uint32_t c = __float_as_uint(cf + 8388608.0f) & 0x7FFFFFu;
+        const uint32_t region = exact_decision(a, b, c, qbits >> 11, lam_n, lam_d, nk, next_ref);
+        failed |= region == 3u;
+        s = region == 0u ? -1.0f : (region == 1u ? 1.0f : 0.0f);
+    }
+    af += s;
+    cf += s;
+    bm1 = fmaf(-2.0f, s, bm1);
+}
+
+// The sub-collisions of one node that one Philox block serves, FP32 fast path.
 //
-// Fast path: U's 12-bit prefix gives 1 + q/4096 <= 1 + U < 1 + (q+1)/4096,
-// compared in FP32 with t1 ~ 1 + T1/D and t2 ~ 1 + T2/D.  Their FP32 error
-// is below 7 * 2^-24 (K1 = 2 lam / (N^2 lam_d): two roundings and a 2-ulp
-// __fdividef; one rounding in a*c or b*(b-1); one in each fused
-// multiply-add), so a comparison with the margin delta = 2^-20 = 16 * 2^-24
-// decides exactly what the integer comparison decides;
-// only when a threshold lies within the margin of the chunk's interval does
-// the decision go to the exact 64-bit path (probability ~2^-11).  States are
-// FP32 integers (exact below 2^24; N <= 3 * 65535).  A node within 2C of the
-// uint16 limit takes collide_node_checked instead.
+// 1 + U lies in [1 + q/4096, 1 + (q+1)/4096) and is compared with
+// t1 ~ 1 + T1/D and t2 ~ 1 + T2/D.  Their FP32 error is below 7 * 2^-24:
+// K1 = 2 lam / (N^2 lam_d) carries two roundings and a 2-ulp __fdividef,
+// a*c and b(b-1) one rounding each, each fused multiply-add one.  `lo` and
+// `hi` sit outside U's interval by at least 2^-21 (2^-20 except lo at q = 0),
+// so every comparison they decide is decided exactly as the integer test
+// would; when a threshold lies within that margin of the interval the
+// decision goes to the exact 64-bit path (probability about 2^-11).
+// State: a, b - 1 and c as FP32 integers (exact below 2^24).
+template <int kC>
+__device__ __forceinline__ void fast_block(float &af, float &bm1, float &cf, float K1, float K2,
+                                           uint32_t blk, uint32_t C, const NodeKey &nk,
+                                           const RoundKeys &rk, uint32_t lam_n, uint32_t lam_d,
+                                           uint32_t &next_ref, bool &failed)
+{
+    uint32_t w0 = nk.x, w1 = nk.r, w2 = nk.t, w3 = (kPurposeCollide << 28) | blk;
+    philox4x32_10(w0, w1, w2, w3, rk);
+    const uint32_t left = kC ? 0u : C - blk * kChunksPerBlock;
+#define MCLG_SUB(m)                                                                         \
+    if (kC ? (m < kC) : (uint32_t(m) < left))                                               \
+        fast_sub_collision(af, bm1, cf, K1, K2, chunk12_at11<m>(w0, w1, w2, w3), nk, lam_n, \
+                           lam_d, next_ref, failed);
+    MCLG_SUB(0) MCLG_SUB(1) MCLG_SUB(2) MCLG_SUB(3) MCLG_SUB(4)
+    MCLG_SUB(5) MCLG_SUB(6) MCLG_SUB(7) MCLG_SUB(8) MCLG_SUB(9)
+#undef MCLG_SUB
+}
+
+// C sequential sub-collisions at one node (Sec. III; D1Q3 table of
+// Sec. III.A), same results as collide_node_checked.  A node within 2C of
+// the uint16 limit takes collide_node_checked, which checks every transition.
 __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t &c,
-                                             const NodeKey &nk, uint32_t C, uint32_t lam_n,
-                                             uint32_t lam_d, uint32_t &err)
+                                             const NodeKey &nk, const RoundKeys &rk, uint32_t C,
+                                             uint32_t lam_n, uint32_t lam_d, uint32_t &err)
 {
     const uint32_t N = a + b + c;
     if (N < 2u) return;
@@ -231,62 +307,26 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
         collide_node_checked<false>(a, b, c, nk, C, lam_n, lam_d, err);
         return;
     }
-    const float fN = __uint_as_float(N | 0x4B000000u) - 8388608.0f;  // exact, N < 2^23
-    // __fdividef: within 2 ulp, covered by the comparison margin
+    // exact int -> float through the exponent bits (all values < 2^23)
+    const float fN = __uint_as_float(N | 0x4B000000u) - 8388608.0f;
     const float K1 = __fdividef(float(2u * lam_n), (fN * fN) * float(lam_d));
     const float K2 = K1 * 0.0625f;
-    constexpr float kDelta = 9.5367431640625e-07f;              // 2^-20
-    constexpr float kHi = 2.44140625e-04f + 9.5367431640625e-07f;  // 2^-12 + 2^-20
     float af = __uint_as_float(a | 0x4B000000u) - 8388608.0f;
-    float bf = __uint_as_float(b | 0x4B000000u) - 8388608.0f;
+    float bm1 = __uint_as_float(b | 0x4B000000u) - 8388609.0f;
     float cf = __uint_as_float(c | 0x4B000000u) - 8388608.0f;
     uint32_t next_ref = 0;
     bool failed = false;
-    for (uint32_t blk = 0; blk * kChunksPerBlock < C; ++blk) {
-        uint32_t w0 = nk.x, w1 = nk.r, w2 = nk.t, w3 = (kPurposeCollide << 28) | blk;
-        philox4x32_10(w0, w1, w2, w3, nk.k0, nk.k1);
-        const uint32_t base = blk * kChunksPerBlock;
-        uint32_t qb[kChunksPerBlock];
-        qb[0] = chunk12_at11<0>(w0, w1, w2, w3);
-        qb[1] = chunk12_at11<1>(w0, w1, w2, w3);
-        qb[2] = chunk12_at11<2>(w0, w1, w2, w3);
-        qb[3] = chunk12_at11<3>(w0, w1, w2, w3);
-        qb[4] = chunk12_at11<4>(w0, w1, w2, w3);
-        qb[5] = chunk12_at11<5>(w0, w1, w2, w3);
-        qb[6] = chunk12_at11<6>(w0, w1, w2, w3);
-        qb[7] = chunk12_at11<7>(w0, w1, w2, w3);
-        qb[8] = chunk12_at11<8>(w0, w1, w2, w3);
-        qb[9] = chunk12_at11<9>(w0, w1, w2, w3);
-#pragma unroll
-        for (int m = 0; m < kChunksPerBlock; ++m) {
-            if (base + m >= C) break;
-            const float uq = unit_of_chunk(qb[m]);
-            const float lo = uq - kDelta;   // below 1 + U by more than the error
-            const float hi = uq + kHi;      // above 1 + U by more than the error
-            const float t1 = fmaf(af * cf, K1, 1.0f);
-            const float t2 = fmaf(bf * (bf - 1.0f), K2, t1);
-            const bool down = hi <= t1;
-            const bool up = lo >= t1 && hi <= t2;
-            const bool none = lo >= t2;
-            float s = down ? -1.0f : (up ? 1.0f : 0.0f);
-            if (!(down || up || none)) {
-                const uint32_t region = exact_decision(uint32_t(af), uint32_t(bf), uint32_t(cf),
-                                                       qb[m] >> 11, lam_n, lam_d, nk, next_ref);
-                failed |= region == 3u;
-                s = region == 0u ? -1.0f : (region == 1u ? 1.0f : 0.0f);
-            }
-            af += s;
-            cf += s;
-            bf = fmaf(-2.0f, s, bf);
-        }
+    if (C == 10u) {
+        fast_block<10>(af, bm1, cf, K1, K2, 0u, C, nk, rk, lam_n, lam_d, next_ref, failed);
+    } else {
+        for (uint32_t blk = 0; blk * kChunksPerBlock < C; ++blk)
+            fast_block<0>(af, bm1, cf, K1, K2, blk, C, nk, rk, lam_n, lam_d, next_ref, failed);
     }
-    if (failed) {
-        // a decision hit the refinement cap: report it like the checked path
-        // (the state after an error is unspecified)
-        err |= kErrSampler;
-    }
+    // a decision that hit the refinement cap is reported like the checked path
+    // reports it (the state after an error is unspecified)
+    if (failed) err |= kErrSampler;
     a = __float_as_uint(af + 8388608.0f) & 0x7FFFFFu;
-    b = __float_as_uint(bf + 8388608.0f) & 0x7FFFFFu;
+    b = __float_as_uint(bm1 + 8388609.0f) & 0x7FFFFFu;
     c = __float_as_uint(cf + 8388608.0f) & 0x7FFFFFu;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "mclg_device.cuh"
+
 namespace mclg {
 
 constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain kernel
@@ -37,6 +39,7 @@ struct PlainArgs {
     uint32_t *err;
     uint32_t variant;  // plain-kernel variant (nodes per thread, register bound)
     uint32_t stream;   // 1: pull-stream before colliding, 0: collide only
+    RoundKeys rk;      // Philox round keys of the seed
 };
 
 struct Unit {
@@ -57,6 +60,7 @@ struct PersistentArgs {
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
     uint32_t stream;  // 1: pull-stream before colliding, 0: collide only
+    RoundKeys rk;     // Philox round keys of the seed
 };
 
 struct StatsBuffers {

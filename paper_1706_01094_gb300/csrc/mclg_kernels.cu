@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
         }
         if (uint32_t(j) < e) {
             const NodeKey nk{x0 + uint32_t(j), rid, p.t, p.k0, p.k1};
-            collide_node(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+            collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
         } else {
             a = b = c = 0u;
         }
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(Pe
                     c = bp[i];
                 }
                 const NodeKey nk{x, s_rid[lo], t, p.k0, p.k1};
-                collide_node(a, b, c, nk, p.C, p.lam_n, p.lam_d, err);
+                collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
             }
             om[i] = uint16_t(a);
             o0[i] = uint16_t(b);
