@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10_000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "uneven"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "uneven", "small"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,13 +262,12 @@ def run_gb300(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         ev0.record(stream)
-        if mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1):
+        persistent = mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)
+        if persistent:
             lat.step(args.steps)
-            launches = None
         else:
             for _ in range(args.steps):
                 lat.step(1)
-            launches = args.steps * (wl.replicas if mode == mclg.MODE_PLAIN else 1)
         ev1.record(stream)
         ev1.synchronize()
     lat.sync()
@@ -285,9 +284,15 @@ def run_gb300(args):
     assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
     node_steps = wl.nodes * args.steps
     value = node_steps * world / (t_max / 1e3) / 1e9
-    if launches is None:
-        n_units = None
-        launches = 1 + (0 if wl.replicas == 1 else 0)
+    long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
+    if persistent:
+        # one persistent launch (chunks of 65536 steps) plus, per step, one
+        # batched plain launch for the replicas too long for a CTA
+        launches = -(-args.steps // 65536) + (args.steps if long_replicas else 0)
+    elif mode == mclg.MODE_PLAIN:
+        launches = args.steps * wl.replicas
+    else:
+        launches = args.steps
 
     # end to end through the C ABI with pinned host buffers: every step uploads
     # the state, advances one step and reads the new state back

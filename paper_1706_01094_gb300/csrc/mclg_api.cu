@@ -52,6 +52,7 @@ struct mclg_ctx {
     uint32_t plain_variant = 0;       // plain-kernel variant (autotuned)
     std::vector<Unit> units;
     Unit *d_units = nullptr;
+    uint32_t *d_unit_counter = nullptr;  // work queue of the persistent kernel
     // statistics
     StatsBuffers st{};
     uint64_t stats_count = 0;
@@ -118,6 +119,9 @@ std::vector<Unit> build_units(const mclg_ctx *h, uint32_t cap)
         u.nodes = uint32_t(nodes);
         out.push_back(u);
     }
+    // largest units first: the CTAs pull them from a queue, so the tail is short
+    std::stable_sort(out.begin(), out.end(),
+                     [](const Unit &x, const Unit &y) { return x.nodes > y.nodes; });
     return out;
 }
 
@@ -196,6 +200,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.err = h->d_err;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
     a.rk = make_round_keys(h->seed);
+    a.unit_counter = h->d_unit_counter;
     return a;
 }
 
@@ -265,7 +270,7 @@ mclg_status autotune(mclg_ctx *h)
 // Plain-kernel autotuner: time each vector width on the real input, writing
 // into the buffer the next step overwrites anyway (results do not depend on
 // the width), and keep the fastest.
-mclg_status autotune_plain(mclg_ctx *h, uint32_t mode)
+mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_t k_end)
 {
     h->plain_tuned = true;
     cudaEvent_t e0, e1;
@@ -277,16 +282,18 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode)
     uint16_t *outb = h->d_B[h->cur ^ 1];
     for (uint32_t v = 0; v < kPlainVariants; ++v) {
         h->plain_variant = v;
-        float ms = 0;
-        for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {  // first launch warms up, keep the best of 3
             MCLG_CK(cudaEventRecord(e0, h->stream));
             if (mode == MCLG_MODE_PLAIN)
                 MCLG_CK(plain_per_replica_step(h, in, outb, h->t, h->stream));
             else
-                MCLG_CK(plain_batch_step(h, in, outb, h->t, 0, h->R, h->stream));
+                MCLG_CK(plain_batch_step(h, in, outb, h->t, k_begin, k_end, h->stream));
             MCLG_CK(cudaEventRecord(e1, h->stream));
             MCLG_CK(cudaEventSynchronize(e1));
-            MCLG_CK(cudaEventElapsedTime(&ms, e0, e1));
+            float one = 0;
+            MCLG_CK(cudaEventElapsedTime(&one, e0, e1));
+            if (rep > 0) ms = std::min(ms, one);
         }
         if (ms < best) {
             best = ms;
@@ -438,6 +445,7 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->d_stage);
     cudaFree(h->d_stageNJ);
     cudaFree(h->d_units);
+    cudaFree(h->d_unit_counter);
     cudaFree(h->lay.d_abi_off);
     cudaFree(h->lay.d_rep_off);
     cudaFree(h->lay.d_rep_L);
@@ -538,6 +546,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     if (!alloc((void **)&h->d_B[0], planes) || !alloc((void **)&h->d_B[1], planes) ||
         !alloc((void **)&h->d_err, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_totals, 2 * sizeof(unsigned long long)) ||
+        !alloc((void **)&h->d_unit_counter, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_stage, 3 * S * sizeof(uint16_t)) ||
         !alloc((void **)&h->lay.d_abi_off, replicas * sizeof(uint64_t)) ||
         !alloc((void **)&h->lay.d_rep_off, replicas * sizeof(uint64_t)) ||
@@ -646,7 +655,7 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     const uint32_t mode = effective_mode(h);
     if (mode == MCLG_MODE_PLAIN || mode == 3u) {
         if (!h->plain_tuned) {
-            mclg_status st = autotune_plain(h, mode);
+            mclg_status st = autotune_plain(h, mode, 0, h->R);
             if (st != MCLG_OK) return st;
         }
         for (uint64_t s = 0; s < n_steps; ++s) {
@@ -674,35 +683,45 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
         if (s != MCLG_OK) return s;
     }
     if (!h->plain_tuned && h->n_small < h->R) {
-        // width for the long replicas stepped beside the persistent kernel
-        h->plain_tuned = true;
-        h->plain_variant = 0;
+        // variant for the long replicas, which step with batched plain launches
+        mclg_status st = autotune_plain(h, 3u, h->n_small, h->R);
+        if (st != MCLG_OK) return st;
     }
     const int start = h->cur;
     const int final_buf = int((uint64_t(start) + n_steps) & 1u);
-    MCLG_CK(cudaEventRecord(h->ev_fork, h->stream));
-    if (h->n_small < h->R) {
+    // Long replicas step with one batched plain launch per step.  When they
+    // alone fill the GPU they go first on the handle's stream; otherwise they
+    // run beside the persistent kernel on the second stream.
+    const uint64_t long_nodes = h->lay.P - h->small_chunks * 8u;
+    const bool has_long = h->n_small < h->R;
+    const bool beside = has_long && long_nodes < (uint64_t(1) << 20);
+    cudaStream_t long_stream = beside ? h->aux : h->stream;
+    if (beside) {
+        MCLG_CK(cudaEventRecord(h->ev_fork, h->stream));
         MCLG_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    }
+    if (has_long) {
         int c = start;
         for (uint64_t s = 0; s < n_steps; ++s) {
-            MCLG_CK(plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], h->t + s, h->n_small, h->R, h->aux));
+            MCLG_CK(plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], h->t + s, h->n_small, h->R,
+                                     long_stream));
             c ^= 1;
         }
-        MCLG_CK(cudaEventRecord(h->ev_join, h->aux));
+        if (beside) MCLG_CK(cudaEventRecord(h->ev_join, h->aux));
     }
     // Each CTA reads its own unit into shared memory before it writes the unit
     // back, and units do not overlap, so launches after the first work in place.
     uint64_t done = 0;
     const uint16_t *in = h->d_B[start];
     uint16_t *outb = h->d_B[final_buf];
-    while (done < n_steps) {
+    while (done < n_steps && h->n_small > 0) {
         const uint32_t chunk = uint32_t(std::min<uint64_t>(n_steps - done, 65536u));
         PersistentArgs a = persistent_args(h, in, outb, h->t + done, chunk, h->d_units, h->p_cap);
         MCLG_CK(launch_persistent(a, uint32_t(h->units.size()), h->p_threads, h->stream));
         in = outb;
         done += chunk;
     }
-    if (h->n_small < h->R) MCLG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    if (beside) MCLG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     h->cur = final_buf;
     h->t += n_steps;
     return MCLG_OK;

@@ -11,7 +11,7 @@ namespace mclg {
 constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain kernel
 constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CTA size
 constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
-constexpr uint32_t kMaxUnitNodes = 16384;        // shared-memory capacity of a persistent CTA
+constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
 
 // Device-resident description of the internal replica order.
@@ -57,6 +57,8 @@ struct PersistentArgs {
     const uint32_t *rep_L;
     const uint32_t *rep_id;
     uint32_t cap;  // shared-memory nodes per buffer (>= every unit's nodes)
+    uint32_t n_units;           // units in `units` (set by launch_persistent)
+    uint32_t *unit_counter;     // work-queue counter, zeroed by launch_persistent
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
     uint32_t stream;  // 1: pull-stream before colliding, 0: collide only

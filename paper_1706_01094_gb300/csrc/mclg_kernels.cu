@@ -13,6 +13,8 @@
 // vector load plus two halo values per warp, every write an aligned vector
 // store.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cstdint>
 
 #include "mclg_device.cuh"
@@ -145,9 +147,11 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent kernel: one CTA per work unit (a run of whole replicas of at most
-// `cap` padded nodes), held in shared memory for all n_steps steps.  Two
-// shared buffers alternate; one barrier per step.
+// Persistent kernel: each CTA takes work units (runs of whole replicas of at
+// most `cap` padded nodes, largest first) from an atomic counter and keeps a
+// unit in shared memory for all n_steps steps.  Two shared buffers alternate;
+// one barrier per step.  Each thread updates node pairs (2i, 2i+1), which never
+// straddle a replica because replicas start on multiples of 8 nodes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(PersistentArgs p)
 {
@@ -156,67 +160,80 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(Pe
     __shared__ uint32_t s_lo[kMaxUnitReplicas + 1];  // unit-local replica starts
     __shared__ uint32_t s_L[kMaxUnitReplicas];
     __shared__ uint32_t s_rid[kMaxUnitReplicas];
-
-    const Unit u = p.units[blockIdx.x];
-    const uint32_t nn = u.nodes;  // padded nodes of this unit (multiple of 8)
-    const uint32_t nrep = u.rep_end - u.rep_begin;
-    for (uint32_t k = threadIdx.x; k < nrep; k += blockDim.x) {
-        const uint32_t kk = u.rep_begin + k;
-        s_lo[k] = uint32_t(p.rep_off[kk] - u.node_begin);
-        s_L[k] = p.rep_L[kk];
-        s_rid[k] = p.rep_id[kk];
-    }
-    if (threadIdx.x == 0) s_lo[nrep] = nn;
+    __shared__ uint32_t s_unit;
 
     uint16_t *buf[2] = {smem, smem + 3 * size_t(p.cap)};
-    // Load the unit: 3 planes x nn nodes, 16-byte vectors.
-    for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
-        const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
-        const uint4 val = *reinterpret_cast<const uint4 *>(p.in + plane * p.P + u.node_begin +
-                                                           8u * w);
-        *reinterpret_cast<uint4 *>(buf[0] + plane * p.cap + 8u * w) = val;
-    }
-    __syncthreads();
-
     uint32_t err = 0;
-    int cur = 0;
-    for (uint32_t s = 0; s < p.n_steps; ++s) {
-        const uint32_t t = p.t0 + s;
-        const uint16_t *bm = buf[cur], *b0 = buf[cur] + p.cap, *bp = buf[cur] + 2 * p.cap;
-        uint16_t *om = buf[cur ^ 1], *o0 = buf[cur ^ 1] + p.cap, *op = buf[cur ^ 1] + 2 * p.cap;
-        for (uint32_t i = threadIdx.x; i < nn; i += blockDim.x) {
-            // replica of node i: largest k with s_lo[k] <= i
-            uint32_t lo = 0, hi = nrep;
-            while (hi - lo > 1u) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_lo[mid] <= i) lo = mid; else hi = mid;
-            }
-            const uint32_t base = s_lo[lo], L = s_L[lo], x = i - base;
-            uint32_t a = 0, b = 0, c = 0;
-            if (x < L) {
-                if (kStream) {
-                    a = bm[base + (x + 1u < L ? x + 1u : 0u)];
-                    b = b0[i];
-                    c = bp[base + (x > 0u ? x - 1u : L - 1u)];
-                } else {
-                    a = bm[i];
-                    b = b0[i];
-                    c = bp[i];
-                }
-                const NodeKey nk{x, s_rid[lo], t, p.k0, p.k1};
-                collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
-            }
-            om[i] = uint16_t(a);
-            o0[i] = uint16_t(b);
-            op[i] = uint16_t(c);
-        }
-        cur ^= 1;
+    for (;;) {
+        __syncthreads();  // the previous unit is written back before the tables change
+        if (threadIdx.x == 0) s_unit = atomicAdd(p.unit_counter, 1u);
         __syncthreads();
-    }
-    for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
-        const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
-        const uint4 val = *reinterpret_cast<const uint4 *>(buf[cur] + plane * p.cap + 8u * w);
-        *reinterpret_cast<uint4 *>(p.out + plane * p.P + u.node_begin + 8u * w) = val;
+        const uint32_t ui = s_unit;
+        if (ui >= p.n_units) break;
+        const Unit u = p.units[ui];
+        const uint32_t nn = u.nodes;  // padded nodes of this unit (multiple of 8)
+        const uint32_t nrep = u.rep_end - u.rep_begin;
+        for (uint32_t k = threadIdx.x; k < nrep; k += blockDim.x) {
+            const uint32_t kk = u.rep_begin + k;
+            s_lo[k] = uint32_t(p.rep_off[kk] - u.node_begin);
+            s_L[k] = p.rep_L[kk];
+            s_rid[k] = p.rep_id[kk];
+        }
+        if (threadIdx.x == 0) s_lo[nrep] = nn;
+        // Load the unit: 3 planes x nn nodes, 16-byte vectors.
+        for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
+            const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
+            const uint4 val = *reinterpret_cast<const uint4 *>(p.in + plane * p.P + u.node_begin +
+                                                               8u * w);
+            *reinterpret_cast<uint4 *>(buf[0] + plane * p.cap + 8u * w) = val;
+        }
+        __syncthreads();
+
+        int cur = 0;
+        for (uint32_t s = 0; s < p.n_steps; ++s) {
+            const uint32_t t = p.t0 + s;
+            const uint16_t *bm = buf[cur], *bz = buf[cur] + p.cap, *bp = buf[cur] + 2 * p.cap;
+            uint16_t *om = buf[cur ^ 1], *oz = buf[cur ^ 1] + p.cap, *op = buf[cur ^ 1] + 2 * p.cap;
+            for (uint32_t i = 2u * threadIdx.x; i < nn; i += 2u * blockDim.x) {
+                // replica of node i: largest k with s_lo[k] <= i
+                uint32_t lo = 0, hi = nrep;
+                while (hi - lo > 1u) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_lo[mid] <= i) lo = mid; else hi = mid;
+                }
+                const uint32_t base = s_lo[lo], L = s_L[lo], x = i - base;
+                const bool v0 = x < L, v1 = x + 1u < L;  // padding nodes stay 0
+                const uint32_t bpair = *reinterpret_cast<const uint32_t *>(bz + i);
+                uint32_t a0, c0, a1, c1;
+                if (kStream) {
+                    a0 = v0 ? bm[base + (x + 1u < L ? x + 1u : 0u)] : 0u;
+                    c0 = v0 ? bp[base + (x > 0u ? x - 1u : L - 1u)] : 0u;
+                    a1 = v1 ? bm[base + (x + 2u < L ? x + 2u : 0u)] : 0u;
+                    c1 = v1 ? bp[base + x] : 0u;
+                } else {
+                    a0 = v0 ? bm[i] : 0u;
+                    c0 = v0 ? bp[i] : 0u;
+                    a1 = v1 ? bm[i + 1] : 0u;
+                    c1 = v1 ? bp[i + 1] : 0u;
+                }
+                uint32_t b0 = v0 ? lo16(bpair) : 0u, b1 = v1 ? hi16(bpair) : 0u;
+                const uint32_t rid = s_rid[lo];
+                const NodeKey nk0{x, rid, t, p.k0, p.k1};
+                const NodeKey nk1{x + 1u, rid, t, p.k0, p.k1};
+                collide_node(a0, b0, c0, nk0, p.rk, p.C, p.lam_n, p.lam_d, err);
+                collide_node(a1, b1, c1, nk1, p.rk, p.C, p.lam_n, p.lam_d, err);
+                *reinterpret_cast<uint32_t *>(om + i) = a0 | (a1 << 16);
+                *reinterpret_cast<uint32_t *>(oz + i) = b0 | (b1 << 16);
+                *reinterpret_cast<uint32_t *>(op + i) = c0 | (c1 << 16);
+            }
+            cur ^= 1;
+            __syncthreads();
+        }
+        for (uint32_t v = threadIdx.x; v < 3u * (nn / 8u); v += blockDim.x) {
+            const uint32_t plane = v / (nn / 8u), w = v % (nn / 8u);
+            const uint4 val = *reinterpret_cast<const uint4 *>(buf[cur] + plane * p.cap + 8u * w);
+            *reinterpret_cast<uint4 *>(p.out + plane * p.P + u.node_begin + 8u * w) = val;
+        }
     }
     flag_error(p.err, err);
 }
@@ -451,7 +468,18 @@ cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_
     cudaError_t e = cudaFuncSetAttribute(k_step_persistent,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_step_persistent<<<n_units, threads, smem, s>>>(p);
+    // as many CTAs as can be resident at once; they pull the units
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent, int(threads),
+                                                           smem)) != cudaSuccess)
+        return e;
+    const uint32_t resident = uint32_t(std::max(1, sms * std::max(per_sm, 1)));
+    PersistentArgs a = p;
+    a.n_units = n_units;
+    if ((e = cudaMemsetAsync(a.unit_counter, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    k_step_persistent<<<std::min(n_units, resident), threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
