@@ -15,7 +15,8 @@
  * not depend on the kernel, tile shape or batch composition):
  *   - Random bits: Philox4x32-10, key (seed & 0xffffffff, seed >> 32),
  *     counter (x, r, t, purpose << 28 | block) with x the replica-local node,
- *     r the replica index, t the time step (t < 2^32).
+ *     r the replica index (plus mclg_params.first_replica), t the time step
+ *     (t < 2^32).
  *   - Sub-collision k at node (x, r) and time t draws a uniform real U whose
  *     first 12 bits are bits [12m, 12m+12) (m = k % 10) of the 128-bit block
  *     (x, r, t, k / 10) (word 0 least significant); while U's region is still
@@ -81,9 +82,14 @@ typedef struct {
     uint32_t lambda_den; /* 1 <= lambda_den <= 256 */
     uint32_t flags;      /* MCLG_NO_STREAM | MCLG_STATS */
     uint32_t mode;       /* MCLG_MODE_* */
+    uint32_t first_replica; /* random-stream index of replica 0: replica r draws with index
+                               first_replica + r, so a batch split over several handles or
+                               GPUs, each given the index of its first replica, reproduces
+                               the unsplit batch bit for bit */
 } mclg_params;
 
-/* Defaults: C = 10, lambda = 1, flags 0, mode AUTO (the paper's D1Q3 runs). */
+/* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0 (the
+ * paper's D1Q3 runs). */
 void mclg_default_params(mclg_params *p);
 
 /* Create a handle for `replicas` independent periodic lattices of lengths

@@ -55,13 +55,13 @@ def _load():
             lib.orc_feq.argtypes = [ctypes.c_double, ctypes.c_double, P]
             lib.orc_poisson_inv.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.orc_poisson_inv.restype = u32
-            lib.orc_init.argtypes = [P, u32, u64, P, P, P]
+            lib.orc_init.argtypes = [P, u32, u64, P, P, P, u32]
             lib.orc_init.restype = i32
             lib.orc_decide.argtypes = [u64, u64, u64, u32, P, i32, P]
             lib.orc_decide.restype = i32
             for name in ("orc_step", "orc_literal_step"):
                 fn = getattr(lib, name)
-                fn.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64]
+                fn.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32]
                 fn.restype = i32
             lib.orc_moments.argtypes = [P, u32, P, P, P, P]
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
@@ -102,7 +102,7 @@ def poisson_inv(mu: float, U: float) -> int:
     return int(_load().orc_poisson_inv(float(mu), float(U)))
 
 
-def init(L, seed: int, rho, u) -> tuple[np.ndarray, int]:
+def init(L, seed: int, rho, u, first_replica: int = 0) -> tuple[np.ndarray, int]:
     """n_i(x, 0) ~ Poisson(f_i^eq(rho(x), u(x))); returns (n[3, S] uint16, error bits)."""
     L = _lengths(L)
     S = int(L.sum())
@@ -111,7 +111,8 @@ def init(L, seed: int, rho, u) -> tuple[np.ndarray, int]:
     if rho.size != S or u.size != S:
         raise ValueError("rho and u need one value per node")
     n = np.zeros((3, S), dtype=np.uint16)
-    err = _load().orc_init(_ptr(L), L.size, seed & (2**64 - 1), _ptr(rho), _ptr(u), _ptr(n))
+    err = _load().orc_init(_ptr(L), L.size, seed & (2**64 - 1), _ptr(rho), _ptr(u), _ptr(n),
+                           first_replica)
     return n, int(err)
 
 
@@ -128,24 +129,25 @@ def decide(T1: int, T2: int, D: int, q0: int, refine=()) -> tuple[int, int]:
     return int(region), int(used.value)
 
 
-def _run(fn_name, L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+def _run(fn_name, L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
     L = _lengths(L)
     S = int(L.sum())
     n = np.array(n, dtype=np.uint16, copy=True).reshape(3, S)
     n = np.ascontiguousarray(n)
     fn = getattr(_load(), fn_name)
-    err = fn(_ptr(L), L.size, seed & (2**64 - 1), C, lam[0], lam[1], flags, _ptr(n), t0, n_steps)
+    err = fn(_ptr(L), L.size, seed & (2**64 - 1), C, lam[0], lam[1], flags, _ptr(n), t0, n_steps,
+             first_replica)
     return n, int(err)
 
 
-def step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+def step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
     """Contract-mode time steps (bit-exact reference).  Returns (n, error bits)."""
-    return _run("orc_step", L, seed, n, t0, n_steps, C, lam, flags)
+    return _run("orc_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
 
 
-def literal_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0):
+def literal_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
     """The paper's particle-pick algorithm with its own random stream (distribution reference)."""
-    return _run("orc_literal_step", L, seed, n, t0, n_steps, C, lam, flags)
+    return _run("orc_literal_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
 
 
 def moments(L, n):

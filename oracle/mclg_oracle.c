@@ -135,7 +135,7 @@ uint32_t orc_poisson_inv(double mu, double U)
  * even p and (2, 3) for odd p.  Returns ORC_ERR_OVERFLOW if a count exceeds
  * 65535, 8 for an invalid (rho, u) (negative, non-finite or |u| > 1). */
 int orc_init(const uint32_t *L, uint32_t R, uint64_t seed, const double *rho, const double *u,
-             uint16_t *n)
+             uint16_t *n, uint32_t r0)
 {
     uint32_t key[2];
     seed_key(seed, key);
@@ -156,7 +156,7 @@ int orc_init(const uint32_t *L, uint32_t R, uint64_t seed, const double *rho, co
                 double mup = mu / (double)parts;
                 uint64_t total = 0;
                 for (uint32_t p = 0; p < parts; p++) {
-                    uint32_t ctr[4] = {x, r, p / 2, (PURPOSE_INIT << 28) | i}, w[4];
+                    uint32_t ctr[4] = {x, r0 + r, p / 2, (PURPOSE_INIT << 28) | i}, w[4];
                     orc_philox(ctr, key, w);
                     uint32_t lo = (p % 2 == 0) ? w[0] : w[2];
                     uint32_t hi = (p % 2 == 0) ? w[1] : w[3];
@@ -332,11 +332,12 @@ static void stream(const uint32_t *L, uint32_t R, uint64_t S, const uint16_t *po
 
 /* n_steps time steps from time t0.  n holds the pre-collision occupations
  * n_i(x, t0) on entry and n_i(x, t0 + n_steps) on return.  Collision at
- * (replica r, local node x, time t) draws from Philox counters (x, r, t, .)
- * with key (seed low 32 bits, seed high 32 bits).  Returns ORC_ERR_* bits;
+ * (replica r, local node x, time t) draws from Philox counters (x, r0 + r,
+ * t, .) with key (seed low 32 bits, seed high 32 bits).  Returns ORC_ERR_* bits;
  * after an error the state is unspecified. */
 int orc_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
-             uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps)
+             uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps,
+             uint32_t r0)
 {
     uint32_t key[2];
     seed_key(seed, key);
@@ -351,7 +352,7 @@ int orc_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t 
         for (uint32_t r = 0; r < R; r++) {
             for (uint32_t x = 0; x < L[r]; x++) {
                 uint16_t st[3] = {n[0 * S + off + x], n[1 * S + off + x], n[2 * S + off + x]};
-                err |= collide_node(st, x, r, t, C, lam_n, lam_d, key);
+                err |= collide_node(st, x, r0 + r, t, C, lam_n, lam_d, key);
                 for (int i = 0; i < 3; i++) post[i * S + off + x] = st[i];
             }
             off += L[r];
@@ -401,7 +402,8 @@ static uint32_t uniform_below(word_stream *ws, uint32_t m)
 }
 
 int orc_literal_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
-                     uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps)
+                     uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps,
+                     uint32_t r0)
 {
     uint32_t key[2];
     seed_key(seed, key);
@@ -416,7 +418,7 @@ int orc_literal_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, u
         for (uint32_t r = 0; r < R; r++) {
             for (uint32_t x = 0; x < L[r]; x++) {
                 int64_t cnt[3] = {n[off + x], n[S + off + x], n[2 * S + off + x]};
-                word_stream ws = {x, r, t, 0, 4, {0, 0, 0, 0}, key};
+                word_stream ws = {x, r0 + r, t, 0, 4, {0, 0, 0, 0}, key};
                 uint32_t N = (uint32_t)(cnt[0] + cnt[1] + cnt[2]);
                 for (uint32_t k = 0; k < C && N >= 2; k++) {
                     uint32_t r1 = 1 + uniform_below(&ws, N);

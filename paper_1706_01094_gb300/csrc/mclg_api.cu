@@ -144,6 +144,7 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.err = h->d_err;
     a.variant = h->plain_variant;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.r0 = h->prm.first_replica;
     a.rk = make_round_keys(h->seed);
     return a;
 }
@@ -199,6 +200,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.r0 = h->prm.first_replica;
     a.rk = make_round_keys(h->seed);
     a.unit_counter = h->d_unit_counter;
     return a;
@@ -362,7 +364,8 @@ int init_range(const mclg_ctx *h, const double *rho, const double *u, uint16_t *
             const double part_mu = mu / double(parts);
             uint64_t total = 0;
             for (uint32_t q = 0; q < parts; ++q) {
-                uint32_t w0 = x, w1 = r, w2 = q / 2, w3 = (kPurposeInit << 28) | i;
+                uint32_t w0 = x, w1 = r + h->prm.first_replica, w2 = q / 2,
+                         w3 = (kPurposeInit << 28) | i;
                 philox4x32_10(w0, w1, w2, w3, k0, k1);
                 const uint32_t lo = (q & 1u) ? w2 : w0, hi = (q & 1u) ? w3 : w1;
                 const uint64_t m = ((uint64_t(hi) << 32) | lo) >> 11;
@@ -410,6 +413,7 @@ void mclg_default_params(mclg_params *p)
     p->lambda_den = 1;
     p->flags = 0;
     p->mode = MCLG_MODE_AUTO;
+    p->first_replica = 0;
 }
 
 const char *mclg_status_str(mclg_status s)
@@ -479,6 +483,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         S += L[r];
     }
     if (S >= (uint64_t(1) << 40)) return MCLG_ERR_ARG;
+    if (uint64_t(prm.first_replica) + replicas > (uint64_t(1) << 32)) return MCLG_ERR_ARG;
     if (prm.flags & MCLG_STATS)
         for (uint32_t r = 1; r < replicas; ++r)
             if (L[r] != L[0]) return MCLG_ERR_ARG;

@@ -39,6 +39,7 @@ struct PlainArgs {
     uint32_t *err;
     uint32_t variant;  // plain-kernel variant (nodes per thread, register bound)
     uint32_t stream;   // 1: pull-stream before colliding, 0: collide only
+    uint32_t r0;       // random-stream index of replica id 0
     RoundKeys rk;      // Philox round keys of the seed
 };
 
@@ -62,6 +63,7 @@ struct PersistentArgs {
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
     uint32_t stream;  // 1: pull-stream before colliding, 0: collide only
+    uint32_t r0;      // random-stream index of replica id 0
     RoundKeys rk;     // Philox round keys of the seed
 };
 

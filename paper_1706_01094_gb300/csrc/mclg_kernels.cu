@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
             c = ep[j];
         }
         if (uint32_t(j) < e) {
-            const NodeKey nk{x0 + uint32_t(j), rid, p.t, p.k0, p.k1};
+            const NodeKey nk{x0 + uint32_t(j), rid + p.r0, p.t, p.k0, p.k1};
             collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
         } else {
             a = b = c = 0u;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(Pe
                     c1 = v1 ? bp[i + 1] : 0u;
                 }
                 uint32_t b0 = v0 ? lo16(bpair) : 0u, b1 = v1 ? hi16(bpair) : 0u;
-                const uint32_t rid = s_rid[lo];
+                const uint32_t rid = s_rid[lo] + p.r0;
                 const NodeKey nk0{x, rid, t, p.k0, p.k1};
                 const NodeKey nk1{x + 1u, rid, t, p.k0, p.k1};
                 collide_node(a0, b0, c0, nk0, p.rk, p.C, p.lam_n, p.lam_d, err);

@@ -38,7 +38,7 @@ class MCLGError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("C", ctypes.c_uint32), ("lambda_num", ctypes.c_uint32),
                 ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("mode", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32)]
 
 
 _lib = None
@@ -129,12 +129,12 @@ class Lattice:
     """A handle: `replicas` independent periodic D1Q3 lattices of lengths L."""
 
     def __init__(self, L, seed: int = 1, C: int = 10, lam=(1, 1), flags: int = 0,
-                 mode: int = MODE_AUTO, stream=None):
+                 mode: int = MODE_AUTO, stream=None, first_replica: int = 0):
         self._lib = load()
         self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
         self.S = int(self.L.sum())
         self.seed = int(seed)
-        p = Params(C, lam[0], lam[1], flags, mode)
+        p = Params(C, lam[0], lam[1], flags, mode, first_replica)
         h = ctypes.c_void_p()
         _check(self._lib.mclg_create(_ptr(self.L), self.L.size, self.seed & (2**64 - 1),
                                      ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),

@@ -245,3 +245,18 @@ def test_uneven_full_size_prefix():
         lat.step(2)
         got, _ = lat.get_state()
     assert np.array_equal(got, want)
+
+
+def test_split_batch_with_first_replica_is_bit_exact():
+    """Two handles with first_replica = index of their first replica reproduce one
+    handle over the whole batch (the rule that lets a batch shard over GPUs)."""
+    L = [300, 17, 1024, 64, 5000, 9]
+    n0 = workloads.random_state(L, 18.0, seed=12)
+    whole = run_gpu(L, 3, n0, 5, 11, mode=mclg.MODE_PERSISTENT)
+    cut = 3
+    S0 = sum(L[:cut])
+    a = run_gpu(L[:cut], 3, n0[:, :S0].copy(), 5, 11, mode=mclg.MODE_PLAIN)
+    b = run_gpu(L[cut:], 3, n0[:, S0:].copy(), 5, 11, mode=mclg.MODE_BATCHED, first_replica=cut)
+    assert np.array_equal(np.concatenate([a, b], axis=1), whole)
+    want, err = oracle.step(L[cut:], 3, n0[:, S0:], 5, 11, first_replica=cut)
+    assert err == 0 and np.array_equal(b, want)
