@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10_000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "uneven", "small"])
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "uneven", "small", "fluct"])
+    ap.add_argument("--u", type=float, default=0.2, help="velocity of the fluct workload")
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -141,7 +143,9 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(name: str):
+def make_workload(name: str, args=None):
+    if name == "fluct":
+        return workloads.fluct(u=args.u if args is not None else 0.2)
     return workloads.BY_NAME[name]()
 
 
@@ -249,7 +253,8 @@ def run_gb300(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_1706_01094_gb300 import build, mclg, sharding
     build.build()
-    wl_full = make_workload(args.workload)
+    wl_full = make_workload(args.workload, args)
+    stats_on = wl_full.name == "fluct"
     if wl_full.replicas == 1:
         # independent lattices: rank k runs replica k of an N-lattice ensemble
         wl, first = wl_full, rank
@@ -260,7 +265,7 @@ def run_gb300(args):
             "batched": mclg.MODE_BATCHED}[args.mode]
     stream = torch.cuda.Stream()
     lat = mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
-                       first_replica=first)
+                       first_replica=first, flags=mclg.STATS if stats_on else 0)
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 
@@ -268,20 +273,20 @@ def run_gb300(args):
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up (also runs the persistent autotuner when it applies)
-    lat.step(args.warmup)
+    # warm-up (also runs the persistent autotuner when it applies); the
+    # statistics workload also burns in before its sums start
+    lat.step(args.warmup + (wl.burn_in if stats_on else 0))
     lat.sync()
+    if stats_on:
+        lat.stats_reset()
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         ev0.record(stream)
-        persistent = mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)
-        if persistent:
-            lat.step(args.steps)
-        else:
-            for _ in range(args.steps):
-                lat.step(1)
+        persistent = (mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)) \
+            and not stats_on
+        lat.step(args.steps)  # the library loops over the steps (CUDA graphs where it can)
         ev1.record(stream)
         ev1.synchronize()
     lat.sync()
@@ -303,10 +308,32 @@ def run_gb300(args):
         # one persistent launch (chunks of 65536 steps) plus, per step, one
         # batched plain launch for the replicas too long for a CTA
         launches = -(-args.steps // 65536) + (args.steps if long_replicas else 0)
-    elif mode == mclg.MODE_PLAIN:
+    elif mode == mclg.MODE_PLAIN and not stats_on:
         launches = args.steps * wl.replicas
     else:
-        launches = args.steps
+        launches = args.steps * (4 if stats_on else 1)  # step (+ statistics: 2 passes, count)
+    stats_summary = None
+    if stats_on:
+        st = lat.stats_read()
+        import math
+        rho, u = float(wl.rho[0]), float(wl.u[0])
+        sq = math.sqrt(1.0 + 3.0 * u * u) - 1.0
+        feq = np.array([rho * w * (1 + 3 * v * u + (3 * v * v - 1) * sq)
+                        for w, v in ((1 / 6, -1), (2 / 3, 0), (1 / 6, 1))])
+        var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
+        var64 = st["cov64"][:, [0, 3, 5]]
+        scale = np.sqrt(var64[:, [0, 0, 1]] * var64[:, [1, 2, 2]])
+        cnt = st["count"]
+        mean = st["s1"].sum(axis=0) / (cnt * wl.L[0])
+        stats_summary = {
+            "samples_per_position": cnt,
+            "fp32_var_max_rel_err_vs_fp64": float((np.abs(var32 - var64) / var64).max()),
+            "fp32_cov_max_err_rel_sqrt_var": float((np.abs(st["cov32"][:, [1, 2, 4]]
+                                                           - st["cov64"][:, [1, 2, 4]]) / scale).max()),
+            "mean_over_feq": (mean / feq).tolist(),
+            "var_over_feq_pooled": (var64.mean(axis=0) / feq).tolist(),
+            "feq": feq.tolist(),
+        }
 
     # end to end through the C ABI with pinned host buffers: every step uploads
     # the state, advances one step and reads the new state back
@@ -366,6 +393,7 @@ def run_gb300(args):
                     "steps": e2e_steps,
                     "path": "mclg_set_state(pinned host) + mclg_step(1) + mclg_get_state(pinned host)"},
             "gpu_launches": launches,
+            **({"stats": stats_summary} if stats_summary else {}),
             "ms_per_launch": ms_launch,
             "clocks": clk,
         }

@@ -55,12 +55,20 @@ struct mclg_ctx {
     uint32_t *d_unit_counter = nullptr;  // work queue of the persistent kernel
     // statistics
     StatsBuffers st{};
+    unsigned long long *d_stat_partials = nullptr;  // the step's batch sums (cleared by the merge)
+    // CUDA graphs of kGraphSteps per-step launch sequences, one per starting
+    // buffer parity, for the plain and batched modes and for the long replicas
+    uint32_t *d_t = nullptr;          // time step read by graph-replayed launches
+    cudaStream_t cap = nullptr;       // private stream for graph capture
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    uint32_t graph_kb = 0, graph_ke = 0;  // replica range the graphs step
     uint64_t stats_count = 0;
 };
 
 namespace {
 
 constexpr uint64_t kMaxT = uint64_t(1) << 32;
+constexpr uint32_t kGraphSteps = 32;  // steps per captured graph (even: parity preserved)
 
 mclg_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? MCLG_OK : MCLG_ERR_CUDA; }
 
@@ -145,6 +153,7 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.variant = h->plain_variant;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
     a.r0 = h->prm.first_replica;
+    a.t_dev = nullptr;
     a.rk = make_round_keys(h->seed);
     return a;
 }
@@ -153,10 +162,12 @@ bool streaming(const mclg_ctx *h) { return !(h->prm.flags & MCLG_NO_STREAM); }
 
 // One step over internal replicas [k_begin, k_end) with a single plain launch.
 cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t,
-                             uint32_t k_begin, uint32_t k_end, cudaStream_t s)
+                             uint32_t k_begin, uint32_t k_end, cudaStream_t s,
+                             const uint32_t *t_dev = nullptr)
 {
     if (k_begin >= k_end) return cudaSuccess;
     PlainArgs a = plain_args(h, in, out, t);
+    a.t_dev = t_dev;
     a.g_begin = h->rep_off[k_begin] / 8u;
     a.g_end = (h->rep_off[k_end - 1] + pad8(h->rep_L[k_end - 1])) / 8u;
     if (k_end - k_begin == 1) {
@@ -308,6 +319,81 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
     return MCLG_OK;
 }
 
+// One step of the plain path over internal replicas [kb, ke) from buffer c,
+// plus the statistics of the new field when they are on.  With t_dev set the
+// launches read their time step from the device (t is then an offset).
+cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t ke,
+                           cudaStream_t s, const uint32_t *t_dev)
+{
+    cudaError_t e = plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], t, kb, ke, s, t_dev);
+    if (e != cudaSuccess) return e;
+    if (h->prm.flags & MCLG_STATS)
+        e = launch_stats(h->d_B[c ^ 1], h->lay.P, h->L[0], h->R, pad8(h->L[0]), streaming(h) ? 1 : 0,
+                         h->st, h->d_stat_partials, s);
+    return e;
+}
+
+void drop_graphs(mclg_ctx *h)
+{
+    for (auto &g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Capture kGraphSteps steps starting from buffer c into h->graph[c].
+mclg_status capture_graph(mclg_ctx *h, int c, uint32_t kb, uint32_t ke)
+{
+    if (h->graph_kb != kb || h->graph_ke != ke) {
+        drop_graphs(h);
+        h->graph_kb = kb;
+        h->graph_ke = ke;
+    }
+    if (h->graph[c]) return MCLG_OK;
+    cudaGraph_t g = nullptr;
+    MCLG_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int cc = c;
+    for (uint32_t j = 0; j < kGraphSteps && e == cudaSuccess; ++j) {
+        e = plain_step_seq(h, cc, j, kb, ke, h->cap, h->d_t);
+        cc ^= 1;
+    }
+    if (e == cudaSuccess) e = launch_advance_time(h->d_t, kGraphSteps, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return MCLG_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->graph[c], g, 0);
+    cudaGraphDestroy(g);
+    return cuda_fail(e);
+}
+
+// n_steps steps of the plain path over [kb, ke) on stream s: whole groups of
+// kGraphSteps replay a captured graph, the rest launch directly.  Returns the
+// buffer that holds the result.
+mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32_t kb, uint32_t ke,
+                        cudaStream_t s, int *c_out)
+{
+    uint64_t done = 0;
+    const uint64_t groups = n_steps / kGraphSteps;
+    if (groups > 0) {
+        mclg_status st = capture_graph(h, c, kb, ke);
+        if (st != MCLG_OK) return st;
+        MCLG_CK(launch_set_time(h->d_t, uint32_t(t), s));
+        for (uint64_t g = 0; g < groups; ++g) MCLG_CK(cudaGraphLaunch(h->graph[c], s));
+        done = groups * kGraphSteps;  // even: the parity of c is unchanged
+    }
+    for (; done < n_steps; ++done) {
+        MCLG_CK(plain_step_seq(h, c, t + done, kb, ke, s, nullptr));
+        c ^= 1;
+    }
+    *c_out = c;
+    return MCLG_OK;
+}
+
 uint32_t effective_mode(const mclg_ctx *h)
 {
     if (h->prm.flags & MCLG_STATS) return 3u;  // batched plain: state in HBM after each step
@@ -440,6 +526,8 @@ void mclg_destroy(mclg_handle h)
         cudaStreamSynchronize(h->aux);
         cudaStreamDestroy(h->aux);
     }
+    drop_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     cudaFree(h->d_B[0]);
@@ -450,6 +538,7 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->d_stageNJ);
     cudaFree(h->d_units);
     cudaFree(h->d_unit_counter);
+    cudaFree(h->d_t);
     cudaFree(h->lay.d_abi_off);
     cudaFree(h->lay.d_rep_off);
     cudaFree(h->lay.d_rep_L);
@@ -463,6 +552,7 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->st.m2);
     cudaFree(h->st.m2c);
     cudaFree(h->st.count);
+    cudaFree(h->d_stat_partials);
     delete h;
 }
 
@@ -536,7 +626,9 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(MCLG_ERR_CUDA);
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess) return fail(MCLG_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(MCLG_ERR_CUDA);
     if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(MCLG_ERR_CUDA);
@@ -552,6 +644,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         !alloc((void **)&h->d_err, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_totals, 2 * sizeof(unsigned long long)) ||
         !alloc((void **)&h->d_unit_counter, sizeof(uint32_t)) ||
+        !alloc((void **)&h->d_t, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_stage, 3 * S * sizeof(uint16_t)) ||
         !alloc((void **)&h->lay.d_abi_off, replicas * sizeof(uint64_t)) ||
         !alloc((void **)&h->lay.d_rep_off, replicas * sizeof(uint64_t)) ||
@@ -576,7 +669,8 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
             !alloc((void **)&h->st.mean32c, Lc * 3 * sizeof(float)) ||
             !alloc((void **)&h->st.m2, Lc * 6 * sizeof(float)) ||
             !alloc((void **)&h->st.m2c, Lc * 6 * sizeof(float)) ||
-            !alloc((void **)&h->st.count, sizeof(unsigned long long)))
+            !alloc((void **)&h->st.count, sizeof(unsigned long long)) ||
+            !alloc((void **)&h->d_stat_partials, stats_partials_bytes(Lc, replicas)))
             return fail(MCLG_ERR_NOMEM);
         *out = h;
         st = mclg_stats_reset(h);
@@ -663,19 +757,21 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
             mclg_status st = autotune_plain(h, mode, 0, h->R);
             if (st != MCLG_OK) return st;
         }
-        for (uint64_t s = 0; s < n_steps; ++s) {
-            const uint16_t *in = h->d_B[h->cur];
-            uint16_t *outb = h->d_B[h->cur ^ 1];
-            if (mode == MCLG_MODE_PLAIN)
-                MCLG_CK(plain_per_replica_step(h, in, outb, h->t, h->stream));
-            else
-                MCLG_CK(plain_batch_step(h, in, outb, h->t, 0, h->R, h->stream));
-            h->cur ^= 1;
-            h->t += 1;
-            if (h->prm.flags & MCLG_STATS) {
-                MCLG_CK(launch_stats(h->d_B[h->cur], h->lay.P, h->L[0], h->R, pad8(h->L[0]),
-                                     streaming(h) ? 1 : 0, h->st, h->stream));
-                h->stats_count += h->R;
+        if (mode == 3u || h->R == 1) {
+            // one launch (plus statistics) per step: replay captured graphs
+            int c = h->cur;
+            mclg_status st = plain_steps(h, h->cur, h->t, n_steps, 0, h->R, h->stream, &c);
+            if (st != MCLG_OK) return st;
+            h->cur = c;
+            h->t += n_steps;
+            if (h->prm.flags & MCLG_STATS) h->stats_count += n_steps * h->R;
+        } else {
+            // the per-replica baseline: one launch per replica and step
+            for (uint64_t s = 0; s < n_steps; ++s) {
+                MCLG_CK(plain_per_replica_step(h, h->d_B[h->cur], h->d_B[h->cur ^ 1], h->t,
+                                               h->stream));
+                h->cur ^= 1;
+                h->t += 1;
             }
         }
         return MCLG_OK;
@@ -707,11 +803,8 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     }
     if (has_long) {
         int c = start;
-        for (uint64_t s = 0; s < n_steps; ++s) {
-            MCLG_CK(plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], h->t + s, h->n_small, h->R,
-                                     long_stream));
-            c ^= 1;
-        }
+        mclg_status st = plain_steps(h, start, h->t, n_steps, h->n_small, h->R, long_stream, &c);
+        if (st != MCLG_OK) return st;
         if (beside) MCLG_CK(cudaEventRecord(h->ev_join, h->aux));
     }
     // Each CTA reads its own unit into shared memory before it writes the unit
@@ -776,6 +869,8 @@ mclg_status mclg_stats_reset(mclg_handle h)
     MCLG_CK(cudaMemsetAsync(h->st.m2, 0, Lc * 6 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.m2c, 0, Lc * 6 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.count, 0, sizeof(unsigned long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->d_stat_partials, 0, stats_partials_bytes(uint32_t(Lc), h->R),
+                            h->stream));
     h->stats_count = 0;
     return MCLG_OK;
 }

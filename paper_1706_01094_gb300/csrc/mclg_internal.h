@@ -40,6 +40,7 @@ struct PlainArgs {
     uint32_t variant;  // plain-kernel variant (nodes per thread, register bound)
     uint32_t stream;   // 1: pull-stream before colliding, 0: collide only
     uint32_t r0;       // random-stream index of replica id 0
+    const uint32_t *t_dev;  // if set, the time step is *t_dev + t (graph replays)
     RoundKeys rk;      // Philox round keys of the seed
 };
 
@@ -85,8 +86,12 @@ cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, 
                                     int stream, cudaStream_t s);
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
                            unsigned long long *totals, cudaStream_t s);
+size_t stats_partials_bytes(uint32_t L, uint32_t R);
 cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
-                         int stream, const StatsBuffers &st, cudaStream_t s);
+                         int stream, const StatsBuffers &st, unsigned long long *partials,
+                         cudaStream_t s);
+cudaError_t launch_set_time(uint32_t *t_dev, uint32_t value, cudaStream_t s);
+cudaError_t launch_advance_time(uint32_t *t_dev, uint32_t by, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint32_t *out,
                           cudaStream_t s);
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
         if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
     }
     const uint32_t e = L - x0 < uint32_t(V) ? L - x0 : uint32_t(V);  // valid nodes here
+    const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
 
     uint32_t err = 0;
     uint32_t om[V], o0[V], op[V];
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
             c = ep[j];
         }
         if (uint32_t(j) < e) {
-            const NodeKey nk{x0 + uint32_t(j), rid + p.r0, p.t, p.k0, p.k1};
+            const NodeKey nk{x0 + uint32_t(j), rid + p.r0, t, p.k0, p.k1};
             collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
         } else {
             a = b = c = 0u;
@@ -332,29 +333,38 @@ __global__ void k_moments(const uint16_t *__restrict__ B, uint64_t P, int32_t *_
 
 // Ensemble statistics of the canonical field, per replica-local position x,
 // pooled over R equal-length replicas (contiguous, offset stride `stride`).
-// Block: 32 positions x (blockDim / 32) replica groups; int64 partial sums
-// are reduced in shared memory and added by one thread per position.  The
-// FP32 path merges the step's batch (R samples) into running means and
-// co-moments with compensated (Kahan) accumulation.
-__global__ void k_stats(const uint16_t *__restrict__ B, uint64_t P, uint32_t L, uint32_t R,
-                        uint64_t stride, int stream, StatsBuffers st)
+// Pass 1: a block covers 32 positions x (blockDim / 32) replica groups of one
+// replica slice and adds its partial sums (18 per position) to the step's
+// batch sums batch[x][18] with 64-bit integer atomics (exact, so the result
+// does not depend on their order).  Pass 2 (k_stats_merge): one thread per
+// position adds the batch to the int64 accumulators, merges it into the FP32
+// running means and co-moments and clears it for the next step.
+constexpr int kStatQ = 18;  // 3 sums + 6 products + 9 neighbour products
+
+__global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restrict__ B, uint64_t P,
+                                                       uint32_t L, uint32_t R, uint64_t stride,
+                                                       int stream, uint32_t slices,
+                                                       unsigned long long *__restrict__ batch)
 {
-    constexpr int kQ = 18;  // 3 sums + 6 products + 9 neighbour products
     const uint32_t xl = threadIdx.x & 31u, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
     const uint32_t x = blockIdx.x * 32u + xl;
-    long long acc[kQ];
+    const uint32_t slice = blockIdx.y;
+    const uint32_t r_begin = uint32_t(uint64_t(R) * slice / slices);
+    const uint32_t r_end = uint32_t(uint64_t(R) * (slice + 1) / slices);
+    unsigned long long acc[kStatQ];
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) acc[q] = 0;
+    for (int q = 0; q < kStatQ; ++q) acc[q] = 0;
     if (x < L) {
-        const uint32_t x1 = x + 1u == L ? 0u : x + 1u;            // neighbour position
+        const uint32_t x1 = x + 1u == L ? 0u : x + 1u;  // neighbour position
         const uint32_t xr = stream ? (x + 1u == L ? 0u : x + 1u) : x;
         const uint32_t xlft = stream ? (x == 0u ? L - 1u : x - 1u) : x;
         const uint32_t x1r = stream ? (x1 + 1u == L ? 0u : x1 + 1u) : x1;
         const uint32_t x1l = stream ? (x1 == 0u ? L - 1u : x1 - 1u) : x1;
-        for (uint32_t r = grp; r < R; r += ngrp) {
+        for (uint32_t r = r_begin + grp; r < r_end; r += ngrp) {
             const uint64_t base = r * stride;
-            const long long v0 = B[base + xr], v1 = B[P + base + x], v2 = B[2 * P + base + xlft];
-            const long long w0 = B[base + x1r], w1 = B[P + base + x1], w2 = B[2 * P + base + x1l];
+            const uint32_t v0 = B[base + xr], v1 = B[P + base + x], v2 = B[2 * P + base + xlft];
+            const uint32_t w0 = B[base + x1r], w1 = B[P + base + x1], w2 = B[2 * P + base + x1l];
+            // every product of two uint16 values fits 32 bits
             acc[0] += v0; acc[1] += v1; acc[2] += v2;
             acc[3] += v0 * v0; acc[4] += v0 * v1; acc[5] += v0 * v2;
             acc[6] += v1 * v1; acc[7] += v1 * v2; acc[8] += v2 * v2;
@@ -363,31 +373,47 @@ __global__ void k_stats(const uint16_t *__restrict__ B, uint64_t P, uint32_t L, 
             acc[15] += v2 * w0; acc[16] += v2 * w1; acc[17] += v2 * w2;
         }
     }
-    extern __shared__ long long red[];  // [ngrp][32][kQ]
+    __shared__ unsigned long long red[8][32][kStatQ + 1];  // <= 8 groups; +1 avoids bank conflicts
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) red[(grp * 32u + xl) * kQ + q] = acc[q];
+    for (int q = 0; q < kStatQ; ++q) red[grp][xl][q] = acc[q];
     __syncthreads();
     if (grp != 0 || x >= L) return;
     for (uint32_t g2 = 1; g2 < ngrp; ++g2)
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) acc[q] += red[(g2 * 32u + xl) * kQ + q];
+        for (int q = 0; q < kStatQ; ++q) acc[q] += red[g2][xl][q];
+    unsigned long long *out = batch + uint64_t(x) * kStatQ;
+#pragma unroll
+    for (int q = 0; q < kStatQ; ++q) atomicAdd(out + q, acc[q]);
+}
+
+__global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restrict__ batch,
+                                                     uint32_t L, uint32_t R, StatsBuffers st)
+{
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L) return;
+    long long acc[kStatQ];
+    unsigned long long *in = batch + uint64_t(x) * kStatQ;
+#pragma unroll
+    for (int q = 0; q < kStatQ; ++q) {
+        acc[q] = (long long)in[q];
+        in[q] = 0ull;
+    }
     for (int q = 0; q < 3; ++q) st.s1[3u * x + q] += acc[q];
     for (int q = 0; q < 6; ++q) st.s2[6u * x + q] += acc[3 + q];
     for (int q = 0; q < 9; ++q) st.snb[9u * x + q] += acc[9 + q];
 
     // FP32 path: batch of R samples at this position.  The batch mean and
     // co-moment come from the exact integer sums (one rounding each); the
-    // running values are merged with the pairwise update of Chan et al.
+    // running values are merged with the pairwise update of Chan et al. and
+    // Kahan-compensated additions.
     const float Rb = float(R);
     const float Ma = float(*st.count);  // samples per position before this batch
     const float Mt = Ma + Rb;
-    float mb[3];
-    for (int i = 0; i < 3; ++i) mb[i] = float(acc[i]) / Rb;
     float delta[3];
     for (int i = 0; i < 3; ++i) {
+        const float mb = float(acc[i]) / Rb;
         const float m = st.mean32[3u * x + i];
-        delta[i] = mb[i] - m;
-        // compensated m += delta * Rb / Mt
+        delta[i] = mb - m;
         const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * x + i];
         const float nm = m + inc;
         st.mean32c[3u * x + i] = (nm - m) - inc;
@@ -408,6 +434,9 @@ __global__ void k_stats(const uint16_t *__restrict__ B, uint64_t P, uint32_t L, 
 }
 
 __global__ void k_count_add(unsigned long long *count, uint32_t R) { *count += R; }
+
+__global__ void k_set_time(uint32_t *t_dev, uint32_t value) { *t_dev = value; }
+__global__ void k_advance_time(uint32_t *t_dev, uint32_t by) { *t_dev += by; }
 
 __global__ void k_philox(const uint4 *__restrict__ ctr, uint64_t n, uint32_t k0, uint32_t k1,
                          uint4 *__restrict__ out)
@@ -516,15 +545,38 @@ cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layo
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
-                         int stream, const StatsBuffers &st, cudaStream_t s)
+uint32_t stats_slices(uint32_t R) { return std::min<uint32_t>(16u, std::max<uint32_t>(1u, R / 8u)); }
+
+size_t stats_partials_bytes(uint32_t L, uint32_t R)
 {
-    const uint32_t th = 256;
-    const size_t smem = size_t(th) * 18 * sizeof(long long);
-    k_stats<<<(L + 31) / 32, th, smem, s>>>(B, P, L, R, stride, stream, st);
+    (void)R;
+    return size_t(L) * kStatQ * sizeof(unsigned long long);
+}
+
+cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
+                         int stream, const StatsBuffers &st, unsigned long long *batch,
+                         cudaStream_t s)
+{
+    const uint32_t slices = stats_slices(R);
+    const dim3 grid((L + 31) / 32, slices);
+    k_stats_partial<<<grid, 256, 0, s>>>(B, P, L, R, stride, stream, slices, batch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_stats_merge<<<(L + 255) / 256, 256, 0, s>>>(batch, L, R, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_count_add<<<1, 1, 0, s>>>(st.count, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(uint32_t *t_dev, uint32_t value, cudaStream_t s)
+{
+    k_set_time<<<1, 1, 0, s>>>(t_dev, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_time(uint32_t *t_dev, uint32_t by, cudaStream_t s)
+{
+    k_advance_time<<<1, 1, 0, s>>>(t_dev, by);
     return cudaGetLastError();
 }
 

@@ -260,3 +260,52 @@ def test_split_batch_with_first_replica_is_bit_exact():
     assert np.array_equal(np.concatenate([a, b], axis=1), whole)
     want, err = oracle.step(L[cut:], 3, n0[:, S0:], 5, 11, first_replica=cut)
     assert err == 0 and np.array_equal(b, want)
+
+
+@pytest.mark.parametrize("u", [0.0, 0.2])
+def test_fluctuation_statistics_full_size(u):
+    """512 replicas x 4096 nodes at rho = 50 (the fluctuation workload): the FP32
+    compensated (co)variances agree with the exact int64 -> FP64 ones to 1e-6, and
+    the occupations are Poisson around the entropic equilibrium (Eqs. poisson,
+    Poisson2, corr, D1Q3equil): pooled mean and variance equal f^eq."""
+    wl = workloads.fluct(u=u)
+    f = oracle.feq(50.0, u)
+    with mclg.Lattice(wl.L, seed=wl.seed, flags=mclg.STATS) as lat:
+        lat.init(wl.rho, wl.u)
+        tot0 = lat.totals()
+        lat.step(200)
+        lat.stats_reset()
+        lat.step(400)
+        st = lat.stats_read()
+        assert np.array_equal(lat.totals(), tot0)
+    cnt = st["count"]
+    assert cnt == 400 * wl.replicas
+    var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
+    var64 = st["cov64"][:, [0, 3, 5]]
+    assert (np.abs(var32 - var64) / var64).max() <= 1e-6
+    scale = np.sqrt(var64[:, [0, 0, 1]] * var64[:, [1, 2, 2]])
+    assert (np.abs(st["cov32"][:, [1, 2, 4]] - st["cov64"][:, [1, 2, 4]]) / scale).max() <= 1e-6
+    mean = st["s1"].sum(axis=0) / (cnt * 4096)
+    assert np.allclose(mean, f, rtol=2e-3), (mean, f)
+    assert np.allclose(var64.mean(axis=0), f, rtol=1e-2), (var64.mean(axis=0), f)
+    # correlator of distinct velocities at one node is zero (Eq. corr)
+    corr = st["cov64"][:, [1, 2, 4]].mean(axis=0) / np.sqrt(f[[0, 0, 1]] * f[[1, 2, 2]])
+    assert np.abs(corr).max() < 0.01, corr
+
+
+@pytest.mark.parametrize("mode,L", [(mclg.MODE_AUTO, [777]), (mclg.MODE_BATCHED, [64, 9, 300]),
+                                    (mclg.MODE_PERSISTENT, [5000, 64, 9000, 33])])
+def test_graph_replayed_steps_bit_exact(mode, L):
+    """Per-step launches replayed from captured CUDA graphs (32 steps each), from
+    both buffer parities, with a remainder launched directly."""
+    n0 = workloads.random_state(L, 22.0, seed=sum(L))
+    want, err = oracle.step(L, 17, n0, 40, 1 + 70 + 33)
+    assert err == 0
+    with mclg.Lattice(L, seed=17, mode=mode) as lat:
+        lat.set_state(n0, t=40)
+        lat.step(1)      # odd parity for the next call
+        lat.step(70)     # 2 graph replays + 6 direct steps
+        lat.step(33)     # 1 replay from the other parity + 1 direct step
+        got, t = lat.get_state()
+    assert t == 40 + 104
+    assert np.array_equal(got, want)
