@@ -1,0 +1,134 @@
+"""Physics of the GPU path at scale, against what the paper states (not the oracle).
+
+* Fig. decay / Eqs. OmN, collmatD1Q3, D1Q3relax: the ensemble mean of the
+  non-conserved moment pi relaxes as the mean-field recursion of one binary
+  collision at a time predicts; the closed form with the constant that
+  Eq. 1Ddecay implies (sqrt 8, reading c6) follows it, the printed 2 sqrt 6
+  does not.  Without streaming the system relaxes to the local equilibrium,
+  which lies slightly below the global one (the text after Eq. local).
+* Fig. 1dPoisson (Sec. III.A): with an even number of rest particles at every
+  site that parity never changes; n_0 follows the Poisson law restricted to
+  even values while n_-1 and n_+1 stay Poisson.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1706_01094_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1706_01094_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1706_01094_gb300 import mclg  # noqa: E402
+
+
+def pi_moment(n):
+    """Ensemble mean of pi = sqrt(2) (n_-1 - n_0 / 2 + n_+1) (Sec. IV.A)."""
+    m = n.astype(np.float64).mean(axis=1)
+    return math.sqrt(2.0) * (m[0] - m[1] / 2 + m[2])
+
+
+def mean_field(f, collisions, lam=1.0):
+    """f^(n+1) = f^(n) + Omega^(1)(f^(n)) with Omega^(1) of Eq. collmatD1Q3."""
+    f = np.array(f, dtype=np.float64)
+    rho = f.sum()
+    out = [f.copy()]
+    for _ in range(collisions):
+        d = f[1] ** 2 / 8 - 2 * f[0] * f[2]
+        f = f + lam / rho ** 2 * np.array([d, -2 * d, d])
+        out.append(f.copy())
+    return out
+
+
+def closed_form(pi0, n, rho, const):
+    """Eq. D1Q3relax at u = 0 with the given constant (sqrt 8 or 2 sqrt 6) times rho."""
+    a = const * rho
+    return a * pi0 / (math.exp(n / rho) * (a + pi0) - pi0)
+
+
+@pytest.mark.parametrize("start", [(0, 300, 0), (150, 0, 150)])
+def test_pi_decay_follows_mean_field(start):
+    R, Lr, C, steps = 1000, 1000, 10, 40
+    L = np.full(R, Lr, dtype=np.uint32)
+    n0 = np.tile(np.array(start, dtype=np.uint16)[:, None], (1, R * Lr))
+    rho = float(sum(start))
+    mf = mean_field(start, C * steps)
+    with mclg.Lattice(L, seed=2024) as lat:
+        lat.set_state(n0)
+        measured = [pi_moment(n0)]
+        for _ in range(steps):
+            lat.step(1)
+            n, _ = lat.get_state()
+            measured.append(pi_moment(n))
+    pi0 = measured[0]
+    for k in range(0, steps + 1, 4):
+        f = mf[C * k]
+        pmf = math.sqrt(2.0) * (f[0] - f[1] / 2 + f[2])
+        # fluctuation corrections are O(1); the initial |pi| is 212 or 424
+        assert abs(measured[k] - pmf) < 1.5, (k, measured[k], pmf)
+    # the closed form with sqrt 8 tracks the recursion; 2 sqrt 6 is further off
+    err8 = max(abs(closed_form(pi0, C * k, rho, math.sqrt(8)) - measured[k]) for k in range(steps + 1))
+    err24 = max(abs(closed_form(pi0, C * k, rho, 2 * math.sqrt(6)) - measured[k])
+                for k in range(steps + 1))
+    assert err8 < 2.5 and err24 > 2 * err8, (err8, err24)
+
+
+def test_local_equilibrium_without_streaming_is_below_global():
+    R, Lr, C = 200, 1000, 10
+    L = np.full(R, Lr, dtype=np.uint32)
+    n0 = np.tile(np.array([100, 100, 100], dtype=np.uint16)[:, None], (1, R * Lr))
+    with mclg.Lattice(L, seed=5, flags=mclg.NO_STREAM) as lat:
+        lat.set_state(n0)
+        lat.step(300)
+        n_local, _ = lat.get_state()
+    with mclg.Lattice(L, seed=5) as lat:
+        lat.set_state(n0)
+        lat.step(300)
+        n_global, _ = lat.get_state()
+    # u = 0 on average: pi^eq = 0 globally; the local equilibrium sits O(1) below
+    p_loc, p_glob = pi_moment(n_local), pi_moment(n_global)
+    assert abs(p_glob) < 0.3, p_glob
+    assert -3.0 < p_loc < -0.3, p_loc
+
+
+def test_even_rest_particles_keep_parity_and_restricted_poisson():
+    R, Lr = 2000, 100  # the paper's lattice length, many independent lattices
+    L = np.full(R, Lr, dtype=np.uint32)
+    S = R * Lr
+    g = np.random.default_rng(11)
+    n = np.zeros((3, S), dtype=np.uint16)
+    n[0] = g.poisson(2.0, S)
+    n[2] = g.poisson(2.0, S)
+    z = g.poisson(8.0, 4 * S)
+    n[1] = z[z % 2 == 0][:S]                  # Poisson(8) restricted to even values
+    hist = {0: np.zeros(64), 1: np.zeros(64), 2: np.zeros(64)}
+    with mclg.Lattice(L, seed=3) as lat:
+        lat.set_state(n)
+        lat.step(300)
+        for _ in range(60):
+            lat.step(10)
+            cur, _ = lat.get_state()
+            assert (cur[1] % 2 == 0).all()     # the spurious invariant of Sec. III.A
+            for i in range(3):
+                hist[i] += np.bincount(np.minimum(cur[i], 63), minlength=64)[:64]
+    k = np.arange(64)
+    logfact = np.array([math.lgamma(v + 1) for v in k])
+    for i, mu in ((0, 2.0), (2, 2.0)):
+        p = np.exp(-mu + k * math.log(mu) - logfact)
+        emp = hist[i] / hist[i].sum()
+        sel = p > 1e-3
+        assert np.all(np.abs(emp[sel] - p[sel]) < 0.02 * p[sel] + 3e-4), (i, emp[:8], p[:8])
+    mu = 8.0
+    p = np.where(k % 2 == 0, np.exp(-mu + k * math.log(mu) - logfact), 0.0)
+    p /= p.sum()
+    emp = hist[1] / hist[1].sum()
+    assert emp[1::2].sum() == 0.0
+    sel = p > 1e-3
+    assert np.all(np.abs(emp[sel] - p[sel]) < 0.02 * p[sel] + 3e-4), (emp[:12], p[:12])
