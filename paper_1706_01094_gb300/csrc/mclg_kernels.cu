@@ -461,7 +461,7 @@ static void launch_plain_v(const PlainArgs &p, bool one, dim3 grid, cudaStream_t
 // Plain-kernel variants: (nodes per thread, minimum CTAs per SM).  More
 // nodes per thread give more independent work per thread; a higher CTA bound
 // caps registers for occupancy.  The autotuner picks one per handle.
-static const uint32_t kVariantVec[kPlainVariants] = {1, 1, 1, 2, 2, 4};
+static const uint32_t kVariantVec[kPlainVariants] = {1, 1, 2, 2, 2, 2};
 
 uint32_t plain_variant_vec(uint32_t variant)
 {
@@ -477,12 +477,12 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s)
     const uint64_t threads = chunks * (8u / V);
     const dim3 grid(uint32_t((threads + kPlainThreads - 1) / kPlainThreads));
     switch (p.variant) {
-    case 0: launch_plain_v<1, 4>(p, one, grid, s); break;
-    case 1: launch_plain_v<1, 6>(p, one, grid, s); break;   // <= 40 registers
-    case 2: launch_plain_v<1, 8>(p, one, grid, s); break;   // <= 32 registers
-    case 3: launch_plain_v<2, 4>(p, one, grid, s); break;   // <= 64 registers
-    case 4: launch_plain_v<2, 1>(p, one, grid, s); break;
-    default: launch_plain_v<4, 1>(p, one, grid, s); break;
+    case 0: launch_plain_v<1, 6>(p, one, grid, s); break;   // <= 40 registers
+    case 1: launch_plain_v<1, 8>(p, one, grid, s); break;   // <= 32 registers
+    case 2: launch_plain_v<2, 4>(p, one, grid, s); break;   // <= 64 registers
+    case 3: launch_plain_v<2, 5>(p, one, grid, s); break;   // <= 51 registers
+    case 4: launch_plain_v<2, 6>(p, one, grid, s); break;   // <= 42 registers
+    default: launch_plain_v<2, 1>(p, one, grid, s); break;
     }
     return cudaGetLastError();
 }
