@@ -75,6 +75,7 @@ typedef enum {
 #define MCLG_MODE_AUTO 0u       /* persistent batch where it pays, plain otherwise */
 #define MCLG_MODE_PLAIN 1u      /* one plain-kernel launch per replica and step */
 #define MCLG_MODE_PERSISTENT 2u /* replicas resident on chip for many steps, one launch */
+#define MCLG_MODE_BATCHED 3u    /* one plain-kernel launch per step over all replicas */
 
 typedef struct {
     uint32_t C;          /* sub-collisions per node and step (paper: C = 10, Sec. III.A, IV.A) */

@@ -566,7 +566,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     mclg_default_params(&prm);
     if (p) prm = *p;
     if (prm.lambda_den < 1 || prm.lambda_den > 256 || prm.lambda_num > prm.lambda_den) return MCLG_ERR_ARG;
-    if (prm.mode > 3u || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS))) return MCLG_ERR_ARG;
+    if (prm.mode > MCLG_MODE_BATCHED || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS))) return MCLG_ERR_ARG;
     uint64_t S = 0;
     for (uint32_t r = 0; r < replicas; ++r) {
         if (L[r] == 0 || L[r] > (uint32_t(1) << 31)) return MCLG_ERR_ARG;
