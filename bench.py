@@ -244,6 +244,27 @@ def config_dict(wl, args, world):
                    if per_gpu * 12 > 129e6 else "state L2-resident")}
 
 
+GRAPH_STEPS = 32  # steps per CUDA graph the library replays
+
+
+def graph_launches(steps: int, per_step: int) -> int:
+    """Kernels of `steps` steps replayed from 32-step graphs: per_step kernels per
+    step, one time-advance kernel per graph and one time-set kernel per call."""
+    groups = steps // GRAPH_STEPS
+    return steps * per_step + groups + (1 if groups else 0)
+
+
+def count_launches(steps, wl, mode, persistent, stats_on, mclg):
+    """Our kernels launched by one mclg_step(steps) call, as the library issues them."""
+    if persistent:
+        long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
+        # one persistent launch per 65536 steps, plus the long replicas' batched plain steps
+        return -(-steps // 65536) + (graph_launches(steps, 1) if long_replicas else 0)
+    if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
+        return steps * wl.replicas  # the per-replica baseline, launched directly
+    return graph_launches(steps, 4 if stats_on else 1)  # step (+ statistics: 2 passes, count)
+
+
 def run_gb300(args):
     import torch
     rank, world, local = dist_env()
@@ -303,15 +324,7 @@ def run_gb300(args):
     assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
     nodes_all = wl.nodes * world if wl_full.replicas == 1 else wl_full.nodes
     value = nodes_all * args.steps / (t_max / 1e3) / 1e9
-    long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
-    if persistent:
-        # one persistent launch (chunks of 65536 steps) plus, per step, one
-        # batched plain launch for the replicas too long for a CTA
-        launches = -(-args.steps // 65536) + (args.steps if long_replicas else 0)
-    elif mode == mclg.MODE_PLAIN and not stats_on:
-        launches = args.steps * wl.replicas
-    else:
-        launches = args.steps * (4 if stats_on else 1)  # step (+ statistics: 2 passes, count)
+    launches = count_launches(args.steps, wl, mode, persistent, stats_on, mclg)
     stats_summary = None
     if stats_on:
         st = lat.stats_read()
