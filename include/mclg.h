@@ -146,10 +146,11 @@ uint64_t mclg_time(mclg_handle h);
 
 /* The autotuned launch configuration of the handle (zeros before the first
  * mclg_step): cfg[0] = 100 * nodes per thread of the plain kernel + its
- * variant index (register bound), cfg[1] = threads
- * per persistent CTA, cfg[2] = nodes per persistent work unit, cfg[3] = number
- * of persistent work units. */
-mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[4]);
+ * variant index (register bound), cfg[1] = threads per persistent CTA,
+ * cfg[2] = nodes per persistent work unit, cfg[3] = number of persistent work
+ * units, cfg[4] = persistent register-bound variant (0, 1, 2 = 1, 2, 3 CTAs of
+ * 512 threads per SM), cfg[5] = 0 (reserved). */
+mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6]);
 
 /* Release every resource of the handle.  NULL-safe. */
 void mclg_destroy(mclg_handle h);

@@ -47,7 +47,7 @@ struct mclg_ctx {
     uint32_t sticky = 0;              // device error bits seen so far
     // persistent configuration (autotuned)
     bool tuned = false;
-    uint32_t p_threads = 256, p_cap = 0;
+    uint32_t p_threads = 256, p_cap = 0, p_variant = 1;
     bool plain_tuned = false;
     uint32_t plain_variant = 0;       // plain-kernel variant (autotuned)
     std::vector<Unit> units;
@@ -214,6 +214,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.r0 = h->prm.first_replica;
     a.rk = make_round_keys(h->seed);
     a.unit_counter = h->d_unit_counter;
+    a.variant = h->p_variant;
     return a;
 }
 
@@ -226,10 +227,12 @@ mclg_status autotune(mclg_ctx *h)
     if (h->n_small == 0) return MCLG_OK;
     uint32_t max_small = 0;
     for (uint32_t k = 0; k < h->n_small; ++k) max_small = std::max<uint32_t>(max_small, uint32_t(pad8(h->rep_L[k])));
+    // unit capacities from the longest small replica up to the limit, and CTA
+    // sizes up to one thread per node pair of a unit
     std::vector<uint32_t> caps;
-    for (uint32_t c = 1024; c <= kMaxUnitNodes; c *= 2)
+    for (uint32_t c = 64; c <= kMaxUnitNodes; c *= 2)
         if (c >= max_small) caps.push_back(c);
-    const uint32_t threads_list[] = {128, 256, 512};
+    const uint32_t threads_all[] = {32, 64, 128, 256, 512};
     uint16_t *scratch = nullptr;
     MCLG_CK(cudaMalloc(&scratch, 3 * h->lay.P * sizeof(uint16_t)));
     cudaEvent_t e0, e1;
@@ -237,6 +240,7 @@ mclg_status autotune(mclg_ctx *h)
     MCLG_CK(cudaEventCreate(&e1));
     float best = 1e30f;
     uint32_t best_threads = 256, best_cap = caps.empty() ? kMaxUnitNodes : caps.back();
+    uint32_t best_variant = 1;
     const uint32_t probe_steps = 4;
     for (uint32_t cap : caps) {
         std::vector<Unit> units = build_units(h, cap);
@@ -244,9 +248,12 @@ mclg_status autotune(mclg_ctx *h)
         MCLG_CK(cudaMalloc(&d_units, units.size() * sizeof(Unit)));
         MCLG_CK(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit),
                                 cudaMemcpyHostToDevice, h->stream));
-        for (uint32_t th : threads_list) {
+        for (uint32_t th : threads_all)
+        for (uint32_t pv = 0; pv < kPersistentVariants; ++pv) {
+            if (th > std::max<uint32_t>(32u, cap / 2u)) continue;
             PersistentArgs a = persistent_args(h, h->d_B[h->cur], scratch, h->t, probe_steps,
                                                d_units, cap);
+            a.variant = pv;
             // warm-up, then timed
             MCLG_CK(launch_persistent(a, uint32_t(units.size()), th, h->stream));
             MCLG_CK(cudaEventRecord(e0, h->stream));
@@ -259,6 +266,7 @@ mclg_status autotune(mclg_ctx *h)
                 best = ms;
                 best_threads = th;
                 best_cap = cap;
+                best_variant = pv;
             }
         }
         MCLG_CK(cudaStreamSynchronize(h->stream));
@@ -272,6 +280,7 @@ mclg_status autotune(mclg_ctx *h)
     MCLG_CK(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
     h->p_threads = best_threads;
     h->p_cap = best_cap;
+    h->p_variant = best_variant;
     h->units = build_units(h, best_cap);
     if (h->d_units) cudaFree(h->d_units);
     MCLG_CK(cudaMalloc(&h->d_units, h->units.size() * sizeof(Unit)));
@@ -921,9 +930,11 @@ mclg_status mclg_sync(mclg_handle h)
 
 uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
 
-mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[4])
+mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6])
 {
     if (!h || !cfg) return MCLG_ERR_ARG;
+    cfg[4] = h->tuned ? h->p_variant : 0u;
+    cfg[5] = 0u;
     cfg[0] = h->plain_tuned ? plain_variant_vec(h->plain_variant) * 100u + h->plain_variant : 0u;
     cfg[1] = h->tuned ? h->p_threads : 0u;
     cfg[2] = h->tuned ? h->p_cap : 0u;

@@ -12,6 +12,7 @@ constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain
 constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CTA size
 constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
+constexpr uint32_t kPersistentVariants = 3;      // register bounds of the persistent kernel
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
 
 // Device-resident description of the internal replica order.
@@ -60,6 +61,7 @@ struct PersistentArgs {
     const uint32_t *rep_id;
     uint32_t cap;  // shared-memory nodes per buffer (>= every unit's nodes)
     uint32_t n_units;           // units in `units` (set by launch_persistent)
+    uint32_t variant;           // register bound: 0, 1, 2 = 1, 2, 3 CTAs of 512 threads per SM
     uint32_t *unit_counter;     // work-queue counter, zeroed by launch_persistent
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;

@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
 // one barrier per step.  Each thread updates node pairs (2i, 2i+1), which never
 // straddle a replica because replicas start on multiples of 8 nodes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_step_persistent(PersistentArgs p)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_persistent(PersistentArgs p)
 {
     const bool kStream = p.stream != 0u;
     extern __shared__ __align__(16) uint16_t smem[];
@@ -489,27 +490,40 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s)
 
 size_t persistent_smem_bytes(uint32_t cap) { return 2u * 3u * size_t(cap) * sizeof(uint16_t); }
 
-cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
-                              cudaStream_t s)
+// Persistent-kernel variants: minimum CTAs of kPersistentMaxThreads threads
+// per SM, i.e. register bounds of 128, 64 and 42 per thread.
+template <int kMinBlocks>
+static cudaError_t launch_persistent_v(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
+                                       cudaStream_t s)
 {
-    if (n_units == 0) return cudaSuccess;
     const size_t smem = persistent_smem_bytes(p.cap);
-    cudaError_t e = cudaFuncSetAttribute(k_step_persistent,
+    cudaError_t e = cudaFuncSetAttribute(k_step_persistent<kMinBlocks>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // as many CTAs as can be resident at once; they pull the units
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent, int(threads),
-                                                           smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<kMinBlocks>,
+                                                           int(threads), smem)) != cudaSuccess)
         return e;
     const uint32_t resident = uint32_t(std::max(1, sms * std::max(per_sm, 1)));
     PersistentArgs a = p;
     a.n_units = n_units;
     if ((e = cudaMemsetAsync(a.unit_counter, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_step_persistent<<<std::min(n_units, resident), threads, smem, s>>>(a);
+    k_step_persistent<kMinBlocks><<<std::min(n_units, resident), threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,
+                              cudaStream_t s)
+{
+    if (n_units == 0) return cudaSuccess;
+    switch (p.variant) {
+    case 0: return launch_persistent_v<1>(p, n_units, threads, s);
+    case 1: return launch_persistent_v<2>(p, n_units, threads, s);
+    default: return launch_persistent_v<3>(p, n_units, threads, s);
+    }
 }
 
 cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,

@@ -192,10 +192,11 @@ class Lattice:
         return int(self._lib.mclg_sync(self._h))
 
     def tuning(self) -> dict:
-        cfg = np.zeros(4, dtype=np.uint32)
+        cfg = np.zeros(6, dtype=np.uint32)
         _check(self._lib.mclg_tuning(self._h, _ptr(cfg)), "mclg_tuning")
-        return {"plain_nodes_per_thread": int(cfg[0]), "persistent_threads": int(cfg[1]),
-                "persistent_unit_nodes": int(cfg[2]), "persistent_units": int(cfg[3])}
+        return {"plain_nodes_per_thread": int(cfg[0]) // 100, "plain_variant": int(cfg[0]) % 100,
+                "persistent_threads": int(cfg[1]), "persistent_unit_nodes": int(cfg[2]),
+                "persistent_units": int(cfg[3]), "persistent_variant": int(cfg[4])}
 
     @property
     def t(self) -> int:
