@@ -309,3 +309,62 @@ def test_graph_replayed_steps_bit_exact(mode, L):
         got, t = lat.get_state()
     assert t == 40 + 104
     assert np.array_equal(got, want)
+
+
+def test_near_maximum_occupations_agree_with_oracle():
+    """Occupations near the uint16 limit take the fully checked path: the error flag
+    and, where no transition overflows, the state agree with the oracle."""
+    g = np.random.default_rng(8)
+    for trial in range(6):
+        S = 256
+        n0 = g.integers(60000, 65536, size=(3, S)).astype(np.uint16)
+        n0[:, ::3] = g.integers(0, 30, size=(3, (S + 2) // 3)).astype(np.uint16)
+        want, err = oracle.step([S], 40 + trial, n0, 0, 1, C=1 + trial, flags=oracle.FLAG_NO_STREAM)
+        with mclg.Lattice([S], seed=40 + trial, C=1 + trial, flags=mclg.NO_STREAM) as lat:
+            lat.set_state(n0)
+            lat.step(1)
+            status = lat.sync_status()
+            assert (status == 4) == bool(err & oracle.ERR_OVERFLOW), (trial, status, err)
+            if status == 0:
+                got, _ = lat.get_state()
+                assert np.array_equal(got, want)
+
+
+def test_largest_masses_without_overflow():
+    # (a, b, c) = (65535, 1, 65535): only {-1,+1} -> {0,0} can happen and b stays small
+    S = 64
+    n0 = np.tile(np.array([[65535], [1], [65535]], dtype=np.uint16), (1, S))
+    want, err = oracle.step([S], 9, n0, 0, 1, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    got = run_gpu([S], 9, n0, 0, 1, flags=mclg.NO_STREAM)
+    assert np.array_equal(got, want)
+
+
+def test_time_limit_and_equal_rationals():
+    L = [100, 7]
+    n0 = workloads.random_state(L, 30.0, seed=2)
+    t0 = 2**32 - 5
+    want, err = oracle.step(L, 4, n0, t0, 5)
+    assert err == 0
+    with mclg.Lattice(L, seed=4) as lat:
+        lat.set_state(n0, t=t0)
+        with pytest.raises(mclg.MCLGError):
+            lat.step(6)                      # would pass t = 2^32
+        lat.step(5)
+        got, t = lat.get_state()
+        assert t == 2**32 and np.array_equal(got, want)
+    a = run_gpu(L, 4, n0, 3, 20, lam=(1, 1))
+    b = run_gpu(L, 4, n0, 3, 20, lam=(256, 256), mode=mclg.MODE_PERSISTENT)
+    assert np.array_equal(a, b)
+
+
+def test_degenerate_and_empty_nodes():
+    L = [8, 1, 2]
+    n0 = np.zeros((3, 11), dtype=np.uint16)
+    n0[:, 1] = [0, 1, 0]
+    n0[:, 8] = [1, 0, 0]                     # the single-node replica
+    n0[:, 9:] = [[2, 0], [0, 3], [0, 0]]
+    for mode in (mclg.MODE_PLAIN, mclg.MODE_PERSISTENT, mclg.MODE_BATCHED):
+        want, err = oracle.step(L, 6, n0, 0, 7)
+        assert err == 0
+        assert np.array_equal(run_gpu(L, 6, n0, 0, 7, mode=mode), want)

@@ -321,3 +321,22 @@ def test_stats_sums_small_case():
     samples0 = np.concatenate([v[0, :, 1], v[0, :, 1]])
     samples2 = np.concatenate([v[2, :, 1], v[2, :, 1]])
     assert abs(cov - np.cov(samples0, samples2, bias=True)[0, 1]) < 1e-12
+
+
+def test_equal_rationals_give_identical_trajectories():
+    """lambda = 256/256 and 1/1 define the same thresholds T/D, so the exact sampler
+    makes the same decisions from the same bits (Sec. III.A with lambda = 1)."""
+    L, n = _rand_case(6, R=3, mean=40)
+    a, err1 = oracle.step(L, 21, n, 0, 12, lam=(1, 1))
+    b, err2 = oracle.step(L, 21, n, 0, 12, lam=(256, 256))
+    c, err3 = oracle.step(L, 21, n, 0, 12, lam=(3, 7))
+    assert err1 == err2 == err3 == 0
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_degenerate_nodes_are_left_alone():
+    """N < 2: no pair can collide (and no random bits are drawn)."""
+    L = [6]
+    n = np.array([[0, 1, 0, 0, 0, 1], [0, 0, 1, 0, 0, 0], [0, 0, 0, 1, 0, 0]], dtype=np.uint16)
+    out, err = oracle.step(L, 1, n, 0, 3, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0 and np.array_equal(out, n)
