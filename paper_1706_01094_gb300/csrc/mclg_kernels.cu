@@ -242,51 +242,85 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_pers
 
 // ---------------------------------------------------------------------------
 // Layout conversions between the ABI field n[3][S] (canonical, replica order)
-// and the pre-streamed device form.  One thread per node.
+// and the pre-streamed device form, and the node moments.  One thread per
+// 8-node chunk of the device form: the replica tables are read once per
+// chunk, the device side moves 16-byte vectors, the ABI side (arbitrary
+// offsets) moves uint16 values, consecutive across the warp.
 // ---------------------------------------------------------------------------
+struct ChunkInfo {
+    uint64_t base;  // device-form offset of the replica
+    uint64_t a0;    // ABI offset of the replica
+    uint32_t L, x0; // replica length, replica-local first node of the chunk
+};
+
+__device__ __forceinline__ ChunkInfo chunk_info(uint64_t g, const uint64_t *abi_off,
+                                                const uint64_t *rep_off, const uint32_t *rep_L,
+                                                const uint32_t *chunk_rep, const uint32_t *rep_id)
+{
+    const uint32_t k = chunk_rep[g];
+    ChunkInfo c;
+    c.base = rep_off[k];
+    c.L = rep_L[k];
+    c.a0 = abi_off[rep_id[k]];
+    c.x0 = uint32_t(g * 8u - c.base);
+    return c;
+}
+
 __global__ void k_to_device_form(const uint16_t *__restrict__ n, uint64_t S, uint16_t *__restrict__ B,
                                  uint64_t P, const uint64_t *__restrict__ abi_off,
                                  const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
-                                 const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                                 const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
                                  const uint32_t *__restrict__ rep_id, int stream)
 {
-    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nodes_padded) return;
-    const uint32_t k = chunk_rep[i / 8u];
-    const uint32_t L = rep_L[k];
-    const uint64_t y = i - rep_off[k];
-    if (y >= L) {
-        B[i] = 0; B[P + i] = 0; B[2 * P + i] = 0;
-        return;
+    const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= chunks) return;
+    const ChunkInfo c = chunk_info(g, abi_off, rep_off, rep_L, chunk_rep, rep_id);
+    uint32_t em[8], ez[8], ep[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t y = c.x0 + uint32_t(j);
+        if (y < c.L) {
+            // B_-1(y) = n_-1(y - 1), B_0(y) = n_0(y), B_+1(y) = n_+1(y + 1)
+            const uint32_t ym = stream ? (y == 0u ? c.L - 1u : y - 1u) : y;
+            const uint32_t yp = stream ? (y + 1u == c.L ? 0u : y + 1u) : y;
+            em[j] = n[c.a0 + ym];
+            ez[j] = n[S + c.a0 + y];
+            ep[j] = n[2 * S + c.a0 + yp];
+        } else {
+            em[j] = ez[j] = ep[j] = 0u;  // padding
+        }
     }
-    const uint64_t a0 = abi_off[rep_id[k]];
-    // B_-1(y) = n_-1(y - 1), B_0(y) = n_0(y), B_+1(y) = n_+1(y + 1)
-    const uint64_t ym = stream ? (y == 0 ? L - 1 : y - 1) : y;
-    const uint64_t yp = stream ? (y + 1 == L ? 0 : y + 1) : y;
-    B[i] = n[a0 + ym];
-    B[P + i] = n[S + a0 + y];
-    B[2 * P + i] = n[2 * S + a0 + yp];
+    uint4 v;
+    pack(em, v);
+    *reinterpret_cast<uint4 *>(B + g * 8u) = v;
+    pack(ez, v);
+    *reinterpret_cast<uint4 *>(B + P + g * 8u) = v;
+    pack(ep, v);
+    *reinterpret_cast<uint4 *>(B + 2 * P + g * 8u) = v;
 }
 
 __global__ void k_from_device_form(const uint16_t *__restrict__ B, uint64_t P, uint16_t *__restrict__ n,
                                    uint64_t S, const uint64_t *__restrict__ abi_off,
                                    const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
-                                   const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                                   const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
                                    const uint32_t *__restrict__ rep_id, int stream)
 {
-    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nodes_padded) return;
-    const uint32_t k = chunk_rep[i / 8u];
-    const uint32_t L = rep_L[k];
-    const uint64_t x = i - rep_off[k];
-    if (x >= L) return;
-    const uint64_t base = rep_off[k];
-    const uint64_t a0 = abi_off[rep_id[k]];
-    const uint64_t xr = stream ? (x + 1 == L ? 0 : x + 1) : x;
-    const uint64_t xl = stream ? (x == 0 ? L - 1 : x - 1) : x;
-    n[a0 + x] = B[base + xr];
-    n[S + a0 + x] = B[P + base + x];
-    n[2 * S + a0 + x] = B[2 * P + base + xl];
+    const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= chunks) return;
+    const ChunkInfo c = chunk_info(g, abi_off, rep_off, rep_L, chunk_rep, rep_id);
+    uint32_t ez[8];
+    unpack(*reinterpret_cast<const uint4 *>(B + P + g * 8u), ez);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t x = c.x0 + uint32_t(j);
+        if (x < c.L) {
+            const uint32_t xr = stream ? (x + 1u == c.L ? 0u : x + 1u) : x;
+            const uint32_t xl = stream ? (x == 0u ? c.L - 1u : x - 1u) : x;
+            n[c.a0 + x] = B[c.base + xr];
+            n[S + c.a0 + x] = uint16_t(ez[j]);
+            n[2 * S + c.a0 + x] = B[2 * P + c.base + xl];
+        }
+    }
 }
 
 // Node moments N = a + b + c, J = c - a of the canonical field, in ABI order,
@@ -294,26 +328,29 @@ __global__ void k_from_device_form(const uint16_t *__restrict__ B, uint64_t P, u
 __global__ void k_moments(const uint16_t *__restrict__ B, uint64_t P, int32_t *__restrict__ N,
                           int32_t *__restrict__ J, const uint64_t *__restrict__ abi_off,
                           const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
-                          const uint32_t *__restrict__ chunk_rep, uint64_t nodes_padded,
+                          const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
                           const uint32_t *__restrict__ rep_id, int stream,
                           unsigned long long *__restrict__ totals)
 {
-    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     long long sn = 0, sj = 0;
-    if (i < nodes_padded) {
-        const uint32_t k = chunk_rep[i / 8u];
-        const uint32_t L = rep_L[k];
-        const uint64_t base = rep_off[k];
-        const uint64_t x = i - base;
-        if (x < L) {
-            const uint64_t xr = stream ? (x + 1 == L ? 0 : x + 1) : x;
-            const uint64_t xl = stream ? (x == 0 ? L - 1 : x - 1) : x;
-            const int32_t a = B[base + xr], b = B[P + base + x], c = B[2 * P + base + xl];
-            const uint64_t o = abi_off[rep_id[k]] + x;
-            if (N) N[o] = a + b + c;
-            if (J) J[o] = c - a;
-            sn = a + b + c;
-            sj = c - a;
+    if (g < chunks) {
+        const ChunkInfo c = chunk_info(g, abi_off, rep_off, rep_L, chunk_rep, rep_id);
+        uint32_t ez[8];
+        unpack(*reinterpret_cast<const uint4 *>(B + P + g * 8u), ez);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t x = c.x0 + uint32_t(j);
+            if (x < c.L) {
+                const uint32_t xr = stream ? (x + 1u == c.L ? 0u : x + 1u) : x;
+                const uint32_t xl = stream ? (x == 0u ? c.L - 1u : x - 1u) : x;
+                const int32_t a = B[c.base + xr], b = int32_t(ez[j]), cc = B[2 * P + c.base + xl];
+                const uint64_t o = c.a0 + x;
+                if (N) N[o] = a + b + cc;
+                if (J) J[o] = cc - a;
+                sn += a + b + cc;
+                sj += cc - a;
+            }
         }
     }
     for (int d = 16; d > 0; d >>= 1) {
@@ -529,10 +566,10 @@ cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_
 cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,
                                   int stream, cudaStream_t s)
 {
-    const uint64_t np = lay.P;
+    const uint64_t chunks = lay.P / 8u;
     const uint32_t th = 256;
-    k_to_device_form<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
-        n, S, B, lay.P, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+    k_to_device_form<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
+        n, S, B, lay.P, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks,
         lay.d_rep_id, stream);
     return cudaGetLastError();
 }
@@ -540,10 +577,10 @@ cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, co
 cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,
                                     int stream, cudaStream_t s)
 {
-    const uint64_t np = lay.P;
+    const uint64_t chunks = lay.P / 8u;
     const uint32_t th = 256;
-    k_from_device_form<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
-        B, lay.P, n, S, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+    k_from_device_form<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
+        B, lay.P, n, S, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks,
         lay.d_rep_id, stream);
     return cudaGetLastError();
 }
@@ -551,10 +588,10 @@ cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, 
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
                            unsigned long long *totals, cudaStream_t s)
 {
-    const uint64_t np = lay.P;
+    const uint64_t chunks = lay.P / 8u;
     const uint32_t th = 256;
-    k_moments<<<uint32_t((np + th - 1) / th), th, 0, s>>>(
-        B, lay.P, N, J, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, np,
+    k_moments<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
+        B, lay.P, N, J, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks,
         lay.d_rep_id, stream, totals);
     return cudaGetLastError();
 }
