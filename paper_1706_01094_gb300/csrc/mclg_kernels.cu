@@ -424,50 +424,56 @@ __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restric
     for (int q = 0; q < kStatQ; ++q) atomicAdd(out + q, acc[q]);
 }
 
+// Pass 2: thread (position, quantity) adds its batch sum to the int64
+// accumulator and clears it; then one thread per position merges the batch
+// into the FP32 running means and co-moments (Chan et al.), with Kahan
+// compensation, reading the batch from shared memory.
+constexpr uint32_t kMergePositions = 14;  // 14 x 18 = 252 threads per block
+
 __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restrict__ batch,
                                                      uint32_t L, uint32_t R, StatsBuffers st)
 {
-    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= L) return;
-    long long acc[kStatQ];
-    unsigned long long *in = batch + uint64_t(x) * kStatQ;
-#pragma unroll
-    for (int q = 0; q < kStatQ; ++q) {
-        acc[q] = (long long)in[q];
-        in[q] = 0ull;
+    __shared__ long long sb[kMergePositions][kStatQ];
+    const uint32_t lp = threadIdx.x / kStatQ, q = threadIdx.x % kStatQ;
+    const uint32_t x = blockIdx.x * kMergePositions + lp;
+    if (lp < kMergePositions && x < L) {
+        unsigned long long *in = batch + uint64_t(x) * kStatQ + q;
+        const long long v = (long long)*in;
+        *in = 0ull;
+        sb[lp][q] = v;
+        if (q < 3) st.s1[3u * x + q] += v;
+        else if (q < 9) st.s2[6u * x + (q - 3)] += v;
+        else st.snb[9u * x + (q - 9)] += v;
     }
-    for (int q = 0; q < 3; ++q) st.s1[3u * x + q] += acc[q];
-    for (int q = 0; q < 6; ++q) st.s2[6u * x + q] += acc[3 + q];
-    for (int q = 0; q < 9; ++q) st.snb[9u * x + q] += acc[9 + q];
-
-    // FP32 path: batch of R samples at this position.  The batch mean and
-    // co-moment come from the exact integer sums (one rounding each); the
-    // running values are merged with the pairwise update of Chan et al. and
-    // Kahan-compensated additions.
+    __syncthreads();
+    if (threadIdx.x >= kMergePositions) return;
+    const uint32_t xm = blockIdx.x * kMergePositions + threadIdx.x;
+    if (xm >= L) return;
+    const long long *acc = sb[threadIdx.x];
     const float Rb = float(R);
     const float Ma = float(*st.count);  // samples per position before this batch
     const float Mt = Ma + Rb;
     float delta[3];
     for (int i = 0; i < 3; ++i) {
         const float mb = float(acc[i]) / Rb;
-        const float m = st.mean32[3u * x + i];
+        const float m = st.mean32[3u * xm + i];
         delta[i] = mb - m;
-        const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * x + i];
+        const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * xm + i];
         const float nm = m + inc;
-        st.mean32c[3u * x + i] = (nm - m) - inc;
-        st.mean32[3u * x + i] = nm;
+        st.mean32c[3u * xm + i] = (nm - m) - inc;
+        st.mean32[3u * xm + i] = nm;
     }
     const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
-    for (int q = 0; q < 6; ++q) {
-        const int i = pi[q], j = pj[q];
+    for (int k = 0; k < 6; ++k) {
+        const int i = pi[k], j = pj[k];
         // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (R s_ij - s_i s_j) / R, exact numerator
-        const long long num = (long long)R * acc[3 + q] - acc[i] * acc[j];
+        const long long num = (long long)R * acc[3 + k] - acc[i] * acc[j];
         const float cb = float(num) / Rb;
-        const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * x + q];
-        const float m2 = st.m2[6u * x + q];
+        const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * xm + k];
+        const float m2 = st.m2[6u * xm + k];
         const float nm2 = m2 + inc;
-        st.m2c[6u * x + q] = (nm2 - m2) - inc;
-        st.m2[6u * x + q] = nm2;
+        st.m2c[6u * xm + k] = (nm2 - m2) - inc;
+        st.m2[6u * xm + k] = nm2;
     }
 }
 
@@ -613,7 +619,7 @@ cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, 
     k_stats_partial<<<grid, 256, 0, s>>>(B, P, L, R, stride, stream, slices, batch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_stats_merge<<<(L + 255) / 256, 256, 0, s>>>(batch, L, R, st);
+    k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, R, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_count_add<<<1, 1, 0, s>>>(st.count, R);
     return cudaGetLastError();

@@ -368,3 +368,24 @@ def test_degenerate_and_empty_nodes():
         want, err = oracle.step(L, 6, n0, 0, 7)
         assert err == 0
         assert np.array_equal(run_gpu(L, 6, n0, 0, 7, mode=mode), want)
+
+
+@pytest.mark.parametrize("Lc,R", [(100, 16), (33, 5), (1, 3)])
+def test_statistics_ragged_lengths_exact(Lc, R):
+    """Statistics for lengths that leave part of a 32-position tile empty."""
+    L = np.full(R, Lc, dtype=np.uint32)
+    n0 = workloads.random_state(L, 9.0, seed=Lc)
+    ref = oracle.Stats(Lc, R)
+    n = n0
+    for k in range(40):
+        n, err = oracle.step(L, 2, n, k, 1)
+        ref.accumulate(n)
+    with mclg.Lattice(L, seed=2, flags=mclg.STATS) as lat:
+        lat.set_state(n0, t=0)
+        lat.stats_reset()
+        lat.step(40)
+        st = lat.stats_read()
+    assert st["count"] == ref.count
+    assert np.array_equal(st["s1"], ref.s1)
+    assert np.array_equal(st["s2"], ref.s2)
+    assert np.array_equal(st["snb"], ref.snb)
