@@ -63,6 +63,12 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32]
                 fn.restype = i32
+            lib.orc_slice_step.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32]
+            lib.orc_slice_step.restype = i32
+            lib.orc_slice_cdf.argtypes = [u32, ctypes.c_int32, u32, u32, u32, u32, P, P, P]
+            lib.orc_slice_cdf.restype = i32
+            lib.orc_slice_draw.argtypes = [u32, ctypes.c_int32, u32, u64, u32, u32, u32]
+            lib.orc_slice_draw.restype = ctypes.c_int64
             lib.orc_moments.argtypes = [P, u32, P, P, P, P]
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
             lib.orc_exact_cov.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, u64]
@@ -148,6 +154,29 @@ def step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
 def literal_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
     """The paper's particle-pick algorithm with its own random stream (distribution reference)."""
     return _run("orc_literal_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
+
+
+def slice_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
+    """Time steps with the slice sampler (the C sub-collisions of a node drawn at
+    once from their exact joint law).  Returns (n, error bits)."""
+    return _run("orc_slice_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
+
+
+def slice_cdf(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):
+    """(F, dmin, dmax): F[d + C] = floor(CDF[d] 2^64) (capped at 2^64 - 1) of the
+    C-step law of the rest count from b on the (N, J) slice."""
+    F = np.zeros(2 * C + 1, dtype=np.uint64)
+    dmin, dmax = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = _load().orc_slice_cdf(N, J, b, C, lam[0], lam[1], _ptr(F), ctypes.byref(dmin),
+                               ctypes.byref(dmax))
+    if rc != 0:
+        raise ValueError("C too large for the slice sampler")
+    return F, int(dmin.value), int(dmax.value)
+
+
+def slice_draw(N: int, J: int, b: int, Q: int, C: int = 10, lam=(1, 1)) -> int:
+    """New rest count of one node from the 64-bit prefix Q of its uniform (-1: undecided)."""
+    return int(_load().orc_slice_draw(N, J, b, Q, C, lam[0], lam[1]))
 
 
 def moments(L, n):

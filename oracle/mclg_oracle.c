@@ -33,6 +33,9 @@
  *   orc_init          pinned: sample mean/variance against Eq. D1Q3equil.
  *   orc_moments       pinned: hand-computed small cases.
  *   orc_stats_*       pinned: hand-computed small cases; numpy cross-check.
+ *   orc_slice_*       pinned: rational matrix powers of the one-sub-collision
+ *                     matrix (N <= 10, and N = 150 by propagated fractions);
+ *                     one-step law by chi-square; invariants.
  */
 #include <math.h>
 #include <stdint.h>
@@ -510,4 +513,241 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
     __int128 num = (__int128)M * sij - (__int128)si * sj;
     long double d = (long double)M * (long double)M;
     return (double)((long double)num / d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Slice sampler: the C sub-collisions of one node drawn at once.            */
+/*                                                                          */
+/* Mass N and momentum J are fixed by the collisions, so a node moves on the */
+/* (N, J) slice, indexed by its rest count b (a = (N-J-b)/2, c = (N+J-b)/2). */
+/* One sub-collision moves b to b+2 with probability T1(b)/D, to b-2 with    */
+/* T_up(b)/D, else keeps it (thresholds of the sequential sampler above).    */
+/* The law after C sub-collisions is the C-th power of that matrix: integer  */
+/* numerators over D^C, computed here by plain dynamic programming in big    */
+/* integers.  The node then takes b' = b + 2 d with d the first offset whose */
+/* cumulative probability CDF[d] exceeds a uniform U.                        */
+/*                                                                          */
+/* Contract: U's first 64 bits are Q = w1 2^32 + w0 with (w0, w1) = words    */
+/* (0, 1) of Philox block (x/2, r, t, PURPOSE_SLICE << 28) for even x and    */
+/* words (2, 3) for odd x; F[d] = min(floor(CDF[d] 2^64), 2^64 - 1); for d in */
+/* [dmin, dmax) (the reachable range, CDF[dmax] = 1) U >= CDF[d] when         */
+/* Q > F[d], U < CDF[d] when Q < F[d]; Q == F[d] is reported as              */
+/* ORC_ERR_SAMPLER (probability below 2^-59 per node-step).  C <= 10.        */
+/* ------------------------------------------------------------------------ */
+#define PURPOSE_SLICE 4u
+#define SLICE_MAX_C 10
+#define BN_LIMBS 20 /* 640-bit unsigned integers in 32-bit limbs */
+
+typedef struct {
+    uint32_t w[BN_LIMBS]; /* least significant limb first */
+} bignum;
+
+static void bn_set(bignum *a, uint64_t v)
+{
+    memset(a->w, 0, sizeof(a->w));
+    a->w[0] = (uint32_t)v;
+    a->w[1] = (uint32_t)(v >> 32);
+}
+
+static void bn_add(bignum *r, const bignum *a)
+{
+    uint64_t carry = 0;
+    for (int i = 0; i < BN_LIMBS; i++) {
+        uint64_t s = (uint64_t)r->w[i] + a->w[i] + carry;
+        r->w[i] = (uint32_t)s;
+        carry = s >> 32;
+    }
+}
+
+static void bn_sub(bignum *r, const bignum *a) /* r >= a */
+{
+    int64_t borrow = 0;
+    for (int i = 0; i < BN_LIMBS; i++) {
+        int64_t d = (int64_t)r->w[i] - a->w[i] - borrow;
+        borrow = d < 0;
+        r->w[i] = (uint32_t)(d + (borrow ? ((int64_t)1 << 32) : 0));
+    }
+}
+
+static void bn_mul_small(bignum *r, uint64_t m)
+{
+    unsigned __int128 carry = 0;
+    for (int i = 0; i < BN_LIMBS; i++) {
+        unsigned __int128 p = (unsigned __int128)r->w[i] * m + carry;
+        r->w[i] = (uint32_t)p;
+        carry = p >> 32;
+    }
+}
+
+static int bn_cmp(const bignum *a, const bignum *b)
+{
+    for (int i = BN_LIMBS - 1; i >= 0; i--) {
+        if (a->w[i] != b->w[i]) return a->w[i] < b->w[i] ? -1 : 1;
+    }
+    return 0;
+}
+
+static void bn_shl(bignum *a, int bits) /* 0 <= bits < 32 * BN_LIMBS */
+{
+    bignum r;
+    memset(r.w, 0, sizeof(r.w));
+    int limbs = bits / 32, sh = bits % 32;
+    for (int i = BN_LIMBS - 1; i >= limbs; i--) {
+        uint64_t v = (uint64_t)a->w[i - limbs] << sh;
+        if (sh && i - limbs - 1 >= 0) v |= (uint64_t)a->w[i - limbs - 1] >> (32 - sh);
+        r.w[i] = (uint32_t)v;
+    }
+    *a = r;
+}
+
+/* floor(num 2^64 / den) for num <= den, by binary long division. */
+static uint64_t bn_frac64(const bignum *num, const bignum *den)
+{
+    bignum rem = *num;
+    uint64_t q = 0;
+    for (int i = 63; i >= 0; i--) {
+        bn_shl(&rem, 1); /* rem = 2 rem: one more bit of the quotient */
+        q <<= 1;
+        if (bn_cmp(&rem, den) >= 0) {
+            bn_sub(&rem, den);
+            q |= 1;
+        }
+    }
+    return q;
+}
+
+/* Transition thresholds of state b on the (N, J) slice (0 outside it). */
+static void slice_thresholds(int64_t N, int64_t J, int64_t b, uint32_t lam_n, uint64_t *down,
+                             uint64_t *up)
+{
+    int64_t aj = J < 0 ? -J : J;
+    *down = 0;
+    *up = 0;
+    if (b < 0 || b > N - aj || ((N - aj - b) & 1)) return;
+    int64_t a = (N - J - b) / 2, c = (N + J - b) / 2;
+    *down = 16 * (uint64_t)a * (uint64_t)c * lam_n;
+    *up = (b > 0 ? (uint64_t)b * (uint64_t)(b - 1) : 0) * lam_n;
+}
+
+/* F[d + C] = floor(CDF[d] 2^64) for d in [-C, C] and the reachable offsets
+ * [*dmin, *dmax].  Returns 0, or -1 for C > SLICE_MAX_C. */
+int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+                  uint64_t *F, int32_t *dmin, int32_t *dmax)
+{
+    if (C > SLICE_MAX_C) return -1;
+    const int W = 2 * SLICE_MAX_C + 1;
+    int64_t aj = J < 0 ? -(int64_t)J : J;
+    int64_t bmin = (N - aj) & 1;
+    *dmin = (int32_t)(-(int64_t)C > (bmin - (int64_t)b) / 2 ? -(int64_t)C : (bmin - (int64_t)b) / 2);
+    *dmax = (int32_t)((int64_t)C < ((int64_t)N - aj - b) / 2 ? (int64_t)C : ((int64_t)N - aj - b) / 2);
+    if (N < 2) { /* no pair to collide: the law stays at offset 0 */
+        for (int d = -(int)C; d <= (int)C; d++) F[d + (int)C] = d < 0 ? 0 : UINT64_MAX;
+        return 0;
+    }
+    uint64_t D = 8 * (uint64_t)N * N * lam_d;
+    bignum v[2 * SLICE_MAX_C + 1], nv[2 * SLICE_MAX_C + 1], den;
+    for (int i = 0; i < W; i++) bn_set(&v[i], 0);
+    bn_set(&v[SLICE_MAX_C], 1); /* all mass at offset 0 */
+    bn_set(&den, 1);
+    for (uint32_t step = 0; step < C; step++) {
+        for (int i = 0; i < W; i++) {
+            int d = i - SLICE_MAX_C;
+            uint64_t down, up;
+            slice_thresholds(N, J, (int64_t)b + 2 * d, lam_n, &down, &up);
+            bignum stay = v[i];
+            bn_mul_small(&stay, D - down - up);
+            nv[i] = stay;
+            if (i > 0) { /* from b + 2(d-1) by a down move (b grows by 2) */
+                uint64_t dn, upx;
+                slice_thresholds(N, J, (int64_t)b + 2 * (d - 1), lam_n, &dn, &upx);
+                bignum t = v[i - 1];
+                bn_mul_small(&t, dn);
+                bn_add(&nv[i], &t);
+            }
+            if (i < W - 1) { /* from b + 2(d+1) by an up move (b shrinks by 2) */
+                uint64_t dn, upx;
+                slice_thresholds(N, J, (int64_t)b + 2 * (d + 1), lam_n, &dn, &upx);
+                bignum t = v[i + 1];
+                bn_mul_small(&t, upx);
+                bn_add(&nv[i], &t);
+            }
+        }
+        for (int i = 0; i < W; i++) v[i] = nv[i];
+        bn_mul_small(&den, D);
+    }
+    bignum cum;
+    bn_set(&cum, 0);
+    for (int i = 0; i < W; i++) {
+        int d = i - SLICE_MAX_C;
+        bn_add(&cum, &v[i]);
+        if (d < -(int)C || d > (int)C) continue;
+        F[d + (int)C] = bn_cmp(&cum, &den) >= 0 ? UINT64_MAX : bn_frac64(&cum, &den);
+    }
+    return 0;
+}
+
+/* The new rest count of one node, or -1 for an undecided prefix. */
+int64_t orc_slice_draw(uint32_t N, int32_t J, uint32_t b, uint64_t Q, uint32_t C,
+                          uint32_t lam_n, uint32_t lam_d)
+{
+    uint64_t F[2 * SLICE_MAX_C + 1];
+    int32_t dmin, dmax;
+    orc_slice_cdf(N, J, b, C, lam_n, lam_d, F, &dmin, &dmax);
+    int32_t d = dmin;
+    for (int32_t k = dmin; k < dmax; k++) {
+        if (Q == F[k + (int32_t)C]) return -1;
+        if (Q > F[k + (int32_t)C]) d = k + 1;
+    }
+    return (int64_t)b + 2 * d;
+}
+
+int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
+                   uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps,
+                   uint32_t r0)
+{
+    if (C > SLICE_MAX_C) return 8;
+    uint32_t key[2];
+    seed_key(seed, key);
+    uint64_t S = 0;
+    for (uint32_t r = 0; r < R; r++) S += L[r];
+    uint16_t *post = (uint16_t *)malloc(3 * S * sizeof(uint16_t) + 1);
+    if (!post) return 16;
+    int err = 0;
+    for (uint64_t s = 0; s < n_steps; s++) {
+        uint32_t t = (uint32_t)(t0 + s);
+        uint64_t off = 0;
+        for (uint32_t r = 0; r < R; r++) {
+            for (uint32_t x = 0; x < L[r]; x++) {
+                uint32_t a = n[off + x], b = n[S + off + x], c = n[2 * S + off + x];
+                uint32_t N = a + b + c;
+                int32_t J = (int32_t)c - (int32_t)a;
+                if (N >= 2) {
+                    uint32_t ctr[4] = {x / 2, r0 + r, t, PURPOSE_SLICE << 28}, w[4];
+                    orc_philox(ctr, key, w);
+                    uint32_t lo = (x % 2 == 0) ? w[0] : w[2];
+                    uint32_t hi = (x % 2 == 0) ? w[1] : w[3];
+                    uint64_t Q = ((uint64_t)hi << 32) | lo;
+                    int64_t nb = orc_slice_draw(N, J, b, Q, C, lam_n, lam_d);
+                    if (nb < 0) {
+                        err |= ORC_ERR_SAMPLER;
+                    } else {
+                        b = (uint32_t)nb;
+                        a = (uint32_t)(((int64_t)N - J - nb) / 2);
+                        c = (uint32_t)(((int64_t)N + J - nb) / 2);
+                        if (a > 65535 || b > 65535 || c > 65535) err |= ORC_ERR_OVERFLOW;
+                    }
+                }
+                post[off + x] = (uint16_t)a;
+                post[S + off + x] = (uint16_t)b;
+                post[2 * S + off + x] = (uint16_t)c;
+            }
+            off += L[r];
+        }
+        if (flags & ORC_FLAG_NO_STREAM)
+            memcpy(n, post, 3 * S * sizeof(uint16_t));
+        else
+            stream(L, R, S, post, n);
+    }
+    free(post);
+    return err;
 }

@@ -1,0 +1,113 @@
+"""Pins of the oracle's slice sampler (the C sub-collisions of a node drawn at once).
+
+The C-step law of a node on its (N, J) slice is the C-th power of the exact
+one-sub-collision matrix of the paper's particle picks (Sec. III, Sec. III.A).
+The oracle computes it with big-integer dynamic programming; these tests
+compare it with an independent rational matrix power (Python fractions) and
+check the inversion rule and the invariants.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+
+stats = pytest.importorskip("scipy.stats")
+
+
+@pytest.mark.parametrize("C,lam", [(1, Fraction(1)), (3, Fraction(1, 2)), (10, Fraction(1)),
+                                   (10, Fraction(3, 7))])
+def test_cdf_equals_rational_matrix_power(C, lam):
+    for N in range(0, 11):
+        for J in range(-N, N + 1):
+            states, P = exact.transition_matrix(N, J, lam)
+            if not states:
+                continue
+            PC = exact.matpow(P, C)
+            for i, (a, b, c) in enumerate(states):
+                F, dmin, dmax = oracle.slice_cdf(N, J, b, C, (lam.numerator, lam.denominator))
+                # the law over b' = b + 2d, cumulated in increasing d
+                cum = Fraction(0)
+                for d in range(-C, C + 1):
+                    bp = b + 2 * d
+                    for k, s in enumerate(states):
+                        if s[1] == bp:
+                            cum += PC[i][k]
+                    want = min((cum * 2**64).numerator // (cum * 2**64).denominator, 2**64 - 1)
+                    assert int(F[d + C]) == want, (N, J, b, d)
+                reach = [s[1] for k, s in enumerate(states) if PC[i][k] > 0] or [b]
+                assert dmin <= (min(reach) - b) // 2 and dmax >= (max(reach) - b) // 2
+
+
+def test_cdf_matches_large_N_recursion_in_fractions():
+    """N = 150 (the single-lattice density): the big-integer recursion against
+    exact fractions propagated over the same band of states."""
+    N, J, b, C = 150, 7, 99, 10
+    lam = Fraction(1)
+    F, dmin, dmax = oracle.slice_cdf(N, J, b, C)
+    def probs(bb):
+        if bb < 0 or bb > N - abs(J) or (N - abs(J) - bb) % 2:
+            return Fraction(0), Fraction(0)
+        a, c = (N - J - bb) // 2, (N + J - bb) // 2
+        return Fraction(2 * a * c, N * N) * lam, Fraction(bb * (bb - 1), 8 * N * N) * lam
+    dist = {b: Fraction(1)}
+    for _ in range(C):
+        new = {}
+        for bb, p in dist.items():
+            dn, up = probs(bb)
+            new[bb] = new.get(bb, 0) + p * (1 - dn - up)
+            if dn:
+                new[bb + 2] = new.get(bb + 2, 0) + p * dn
+            if up:
+                new[bb - 2] = new.get(bb - 2, 0) + p * up
+        dist = new
+    cum = Fraction(0)
+    for d in range(-C, C + 1):
+        cum += dist.get(b + 2 * d, Fraction(0))
+        want = min(int(cum * 2**64), 2**64 - 1)
+        assert int(F[d + C]) == want, d
+    assert (dmin, dmax) == (-10, 10)
+
+
+@pytest.mark.parametrize("state,C,lam", [((3, 4, 5), 10, (1, 1)), ((0, 9, 1), 4, (1, 2)),
+                                          ((6, 0, 6), 10, (3, 7))])
+def test_slice_step_law_equals_matrix_power(state, C, lam):
+    N, J = sum(state), state[2] - state[0]
+    states, P = exact.transition_matrix(N, J, Fraction(*lam))
+    row = exact.matpow(P, C)[states.index(tuple(state))]
+    probs = np.array([float(p) for p in row])
+    L = np.full(40, 2500, dtype=np.uint32)
+    S = int(L.sum())
+    n = np.tile(np.array(state, dtype=np.uint16)[:, None], (1, S))
+    out, err = oracle.slice_step(L, 77, n, 2, 1, C=C, lam=lam, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    counts = np.zeros(len(states))
+    for s, cnt in zip(*np.unique(out.T, axis=0, return_counts=True)):
+        counts[states.index(tuple(int(v) for v in s))] += cnt
+    exp = probs * S
+    keep = exp >= 5
+    chi2 = (((counts[keep] - exp[keep]) ** 2) / exp[keep]).sum()
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+
+
+def test_slice_step_invariants():
+    g = np.random.default_rng(1)
+    L = np.array([37, 64, 5], dtype=np.uint32)
+    n = g.poisson(40, size=(3, int(L.sum()))).astype(np.uint16)
+    N0, J0, tot0 = oracle.moments(L, n)
+    out, err = oracle.slice_step(L, 3, n, 0, 1, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    N1, J1, _ = oracle.moments(L, out)
+    assert (N0 == N1).all() and (J0 == J1).all() and (out != n).any()
+    out2, err = oracle.slice_step(L, 3, n, 0, 25)
+    assert err == 0
+    assert np.array_equal(oracle.moments(L, out2)[2], tot0)
+    assert ((out2[1] % 2) == (n[1] % 2)).all()
+    # the single-particle and empty nodes stay as they are
+    tiny = np.array([[0, 1], [1, 0], [0, 0]], dtype=np.uint16)
+    same, err = oracle.slice_step([2], 3, tiny, 0, 4, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0 and np.array_equal(same, tiny)
+    with pytest.raises(ValueError):
+        oracle.slice_cdf(10, 0, 6, C=11)
