@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "uneven", "small", "fluct"])
     ap.add_argument("--u", type=float, default=0.2, help="velocity of the fluct workload")
+    ap.add_argument("--sampler", default="sequential", choices=["sequential", "slice"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,8 +286,10 @@ def run_gb300(args):
     mode = {"auto": mclg.MODE_AUTO, "plain": mclg.MODE_PLAIN, "persistent": mclg.MODE_PERSISTENT,
             "batched": mclg.MODE_BATCHED}[args.mode]
     stream = torch.cuda.Stream()
+    sampler = mclg.SAMPLER_SLICE if args.sampler == "slice" else mclg.SAMPLER_SEQUENTIAL
     lat = mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
-                       first_replica=first, flags=mclg.STATS if stats_on else 0)
+                       first_replica=first, flags=mclg.STATS if stats_on else 0,
+                       sampler=sampler)
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 

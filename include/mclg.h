@@ -64,12 +64,31 @@ typedef enum {
     MCLG_ERR_OVERFLOW = 4, /* an occupation would leave [0, 65535]; state unspecified */
     MCLG_ERR_TIMEOUT = 5,  /* reserved: a bounded device-side wait gave up */
     MCLG_ERR_STATE = 6,    /* no state yet (call mclg_init or mclg_set_state) */
-    MCLG_ERR_SAMPLER = 7   /* a decision stayed open after 4 refinement chunks (p < 2^-70) */
+    MCLG_ERR_SAMPLER = 7,  /* a decision stayed open (sequential: after 4 refinement chunks,
+                              p < 2^-70; slice: the 64-bit prefix hit a table value, p < 2^-59) */
+    MCLG_ERR_RANGE = 8     /* slice sampler: a node's mass exceeds the tables' n_max */
 } mclg_status;
 
 /* flags */
 #define MCLG_NO_STREAM 1u /* collide only, no streaming (the "without streaming" runs of Fig. decay) */
 #define MCLG_STATS 2u     /* accumulate ensemble statistics after every step (Sec. V) */
+
+/* samplers: two exact ways to draw the C sub-collisions of a node, with
+ * different uses of the random bits (each is bit-exact to its own oracle):
+ *   SEQUENTIAL  the paper's order (Sec. III): C decisions one after another,
+ *               each an exact uniform against the thresholds T1/D, T2/D.
+ *   SLICE       all C at once: the rest count b moves to b + 2d with the exact
+ *               C-step law on the node's (N, J) slice (the C-th power of the
+ *               one-sub-collision matrix), inverted with one 64-bit uniform
+ *               prefix Q = w1 2^32 + w0, words (0, 1) of Philox block
+ *               (x/2, r, t, 4 << 28) for even x, words (2, 3) for odd x;
+ *               d = dmin + #{d' in [dmin, dmax) : Q > F[d']} with
+ *               F[d'] = min(floor(CDF[d'] 2^64), 2^64 - 1) over the reachable
+ *               offsets, Q == F[d'] reported as MCLG_ERR_SAMPLER.  Tables of F
+ *               are built exactly (big integers) on the host for masses up to
+ *               n_max; requires C <= 10; runs in the plain and batched modes. */
+#define MCLG_SAMPLER_SEQUENTIAL 0u
+#define MCLG_SAMPLER_SLICE 1u
 
 /* execution modes; every mode gives bit-identical results */
 #define MCLG_MODE_AUTO 0u       /* persistent batch where it pays, plain otherwise */
@@ -87,10 +106,14 @@ typedef struct {
                                first_replica + r, so a batch split over several handles or
                                GPUs, each given the index of its first replica, reproduces
                                the unsplit batch bit for bit */
+    uint32_t sampler;       /* MCLG_SAMPLER_* */
+    uint32_t slice_n_max;   /* SLICE: largest node mass the tables cover (<= 4096); 0 = the
+                               state's largest mass when stepping starts, plus a margin of
+                               32 + 8 sqrt(mass) */
 } mclg_params;
 
-/* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0 (the
- * paper's D1Q3 runs). */
+/* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0,
+ * SEQUENTIAL sampler (the paper's D1Q3 runs). */
 void mclg_default_params(mclg_params *p);
 
 /* Create a handle for `replicas` independent periodic lattices of lengths
@@ -177,6 +200,14 @@ const char *mclg_status_str(mclg_status s);
  * threads on the same device) race: order them on one stream. */
 mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int32_t *J,
                                  int64_t *totals, void *cuda_stream);
+
+/* The slice sampler's table row for the state (N, J, b) (host computation, no
+ * GPU): F[k] = min(floor(CDF[dmin + k] 2^64), 2^64 - 1) for k < dmax - dmin,
+ * the exact cumulative C-step law of the rest count (F holds 2C entries);
+ * *dmin, *dmax the reachable offsets.  For checking the tables against an
+ * independent computation.  MCLG_ERR_ARG for C > 10 or an invalid state. */
+mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
+                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax);
 
 /* Philox4x32-10 of the library's device generator on n counters: ctr and out
  * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For

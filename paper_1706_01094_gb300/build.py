@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmclg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu"]
+SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu", "mclg_slice_table.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
+                           "-Xlinker", "--no-undefined"])
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

@@ -62,6 +62,13 @@ struct mclg_ctx {
     cudaStream_t cap = nullptr;       // private stream for graph capture
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint32_t graph_kb = 0, graph_ke = 0;  // replica range the graphs step
+    // slice sampler: exact cumulative C-step laws for masses up to slice.n_max
+    SliceTables slice{};
+    uint32_t *d_rowstart = nullptr;
+    uint16_t *d_slice_primary = nullptr;
+    unsigned long long *d_slice_secondary = nullptr;
+    unsigned int *d_max_mass = nullptr;
+    bool state_dirty = true;          // a new state: check its masses against the tables
     uint64_t stats_count = 0;
 };
 
@@ -94,6 +101,7 @@ mclg_status status_from_bits(uint32_t bits)
 {
     if (bits & kErrOverflow) return MCLG_ERR_OVERFLOW;
     if (bits & kErrSampler) return MCLG_ERR_SAMPLER;
+    if (bits & kErrRange) return MCLG_ERR_RANGE;
     return MCLG_OK;
 }
 
@@ -170,13 +178,14 @@ cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uin
     a.t_dev = t_dev;
     a.g_begin = h->rep_off[k_begin] / 8u;
     a.g_end = (h->rep_off[k_end - 1] + pad8(h->rep_L[k_end - 1])) / 8u;
-    if (k_end - k_begin == 1) {
+    const bool one = k_end - k_begin == 1;
+    if (one) {
         a.one_off = h->rep_off[k_begin];
         a.one_L = h->rep_L[k_begin];
         a.one_rid = h->order[k_begin];
-        return launch_plain(a, true, s);
     }
-    return launch_plain(a, false, s);
+    if (h->prm.sampler == MCLG_SAMPLER_SLICE) return launch_slice(a, one, h->slice, s);
+    return launch_plain(a, one, s);
 }
 
 // One step with one plain launch per replica (the per-replica baseline).
@@ -403,9 +412,70 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
     return MCLG_OK;
 }
 
+void free_slice_tables(mclg_ctx *h)
+{
+    cudaFree(h->d_rowstart);
+    cudaFree(h->d_slice_primary);
+    cudaFree(h->d_slice_secondary);
+    h->d_rowstart = nullptr;
+    h->d_slice_primary = nullptr;
+    h->d_slice_secondary = nullptr;
+    h->slice = SliceTables{};
+}
+
+// Make sure the slice tables cover every node mass of the current state:
+// build them (exact big-integer laws, host cores) for masses up to n_max.
+mclg_status ensure_slice_tables(mclg_ctx *h)
+{
+    MCLG_CK(launch_max_mass(h->d_B[h->cur], h->lay, streaming(h) ? 1 : 0, h->d_max_mass, h->stream));
+    unsigned int max_mass = 0;
+    MCLG_CK(cudaMemcpyAsync(&max_mass, h->d_max_mass, sizeof(max_mass), cudaMemcpyDeviceToHost,
+                            h->stream));
+    MCLG_CK(cudaStreamSynchronize(h->stream));
+    h->state_dirty = false;
+    if (h->slice.primary && max_mass <= h->slice.n_max) return MCLG_OK;
+    uint32_t n_max = h->prm.slice_n_max;
+    if (n_max == 0)
+        n_max = std::min<uint32_t>(kSliceMaxN, max_mass + 32u +
+                                                   uint32_t(8.0 * std::sqrt(double(max_mass))));
+    if (max_mass > n_max) return MCLG_ERR_RANGE;
+    std::vector<uint32_t> rowstart;
+    std::vector<uint16_t> primary;
+    std::vector<uint64_t> secondary;
+    try {
+        build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den, rowstart, primary,
+                           secondary);
+    } catch (...) {
+        return MCLG_ERR_NOMEM;
+    }
+    MCLG_CK(cudaStreamSynchronize(h->stream));
+    free_slice_tables(h);
+    if (cudaMalloc(&h->d_rowstart, rowstart.size() * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_slice_primary, primary.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_slice_secondary, secondary.size() * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        free_slice_tables(h);
+        return MCLG_ERR_NOMEM;
+    }
+    MCLG_CK(cudaMemcpy(h->d_rowstart, rowstart.data(), rowstart.size() * sizeof(uint32_t),
+                       cudaMemcpyHostToDevice));
+    MCLG_CK(cudaMemcpy(h->d_slice_primary, primary.data(), primary.size() * sizeof(uint16_t),
+                       cudaMemcpyHostToDevice));
+    MCLG_CK(cudaMemcpy(h->d_slice_secondary, secondary.data(), secondary.size() * sizeof(uint64_t),
+                       cudaMemcpyHostToDevice));
+    h->slice.n_max = n_max;
+    h->slice.rowstart = h->d_rowstart;
+    h->slice.primary = h->d_slice_primary;
+    h->slice.secondary = h->d_slice_secondary;
+    drop_graphs(h);  // captured launches hold the old table pointers
+    return MCLG_OK;
+}
+
 uint32_t effective_mode(const mclg_ctx *h)
 {
     if (h->prm.flags & MCLG_STATS) return 3u;  // batched plain: state in HBM after each step
+    if (h->prm.sampler == MCLG_SAMPLER_SLICE)  // the slice kernel has no persistent form
+        return (h->prm.mode == MCLG_MODE_PLAIN || h->R == 1) ? MCLG_MODE_PLAIN : 3u;
     if (h->prm.mode == MCLG_MODE_PLAIN) return MCLG_MODE_PLAIN;
     if (h->prm.mode == MCLG_MODE_PERSISTENT) return MCLG_MODE_PERSISTENT;
     if (h->prm.mode == 3u) return 3u;
@@ -493,6 +563,7 @@ mclg_status upload_state(mclg_ctx *h, const uint16_t *n, uint64_t t)
     h->t = t;
     h->sticky = 0;
     h->has_state = true;
+    h->state_dirty = true;
     return MCLG_OK;
 }
 
@@ -509,6 +580,8 @@ void mclg_default_params(mclg_params *p)
     p->flags = 0;
     p->mode = MCLG_MODE_AUTO;
     p->first_replica = 0;
+    p->sampler = MCLG_SAMPLER_SEQUENTIAL;
+    p->slice_n_max = 0;
 }
 
 const char *mclg_status_str(mclg_status s)
@@ -521,7 +594,8 @@ const char *mclg_status_str(mclg_status s)
     case MCLG_ERR_OVERFLOW: return "occupation overflow (uint16)";
     case MCLG_ERR_TIMEOUT: return "device wait timed out";
     case MCLG_ERR_STATE: return "no state set";
-    case MCLG_ERR_SAMPLER: return "sampler refinement cap reached";
+    case MCLG_ERR_SAMPLER: return "sampler could not decide (refinement cap / table tie)";
+    case MCLG_ERR_RANGE: return "node mass beyond the slice sampler's tables";
     }
     return "unknown status";
 }
@@ -548,6 +622,8 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->d_units);
     cudaFree(h->d_unit_counter);
     cudaFree(h->d_t);
+    cudaFree(h->d_max_mass);
+    free_slice_tables(h);
     cudaFree(h->lay.d_abi_off);
     cudaFree(h->lay.d_rep_off);
     cudaFree(h->lay.d_rep_L);
@@ -583,6 +659,10 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     }
     if (S >= (uint64_t(1) << 40)) return MCLG_ERR_ARG;
     if (uint64_t(prm.first_replica) + replicas > (uint64_t(1) << 32)) return MCLG_ERR_ARG;
+    if (prm.sampler > MCLG_SAMPLER_SLICE) return MCLG_ERR_ARG;
+    if (prm.sampler == MCLG_SAMPLER_SLICE &&
+        (prm.C > uint32_t(kSliceMaxC) || prm.slice_n_max > kSliceMaxN))
+        return MCLG_ERR_ARG;
     if (prm.flags & MCLG_STATS)
         for (uint32_t r = 1; r < replicas; ++r)
             if (L[r] != L[0]) return MCLG_ERR_ARG;
@@ -654,6 +734,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         !alloc((void **)&h->d_totals, 2 * sizeof(unsigned long long)) ||
         !alloc((void **)&h->d_unit_counter, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_t, sizeof(uint32_t)) ||
+        !alloc((void **)&h->d_max_mass, sizeof(unsigned int)) ||
         !alloc((void **)&h->d_stage, 3 * S * sizeof(uint16_t)) ||
         !alloc((void **)&h->lay.d_abi_off, replicas * sizeof(uint64_t)) ||
         !alloc((void **)&h->lay.d_rep_off, replicas * sizeof(uint64_t)) ||
@@ -761,6 +842,13 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     if (n_steps == 0) return MCLG_OK;
     MCLG_CK(cudaSetDevice(h->device));
     const uint32_t mode = effective_mode(h);
+    if (h->prm.sampler == MCLG_SAMPLER_SLICE) {
+        if (h->state_dirty) {
+            mclg_status st = ensure_slice_tables(h);
+            if (st != MCLG_OK) return st;
+        }
+        h->plain_tuned = true;  // the slice kernel has a single variant
+    }
     if (mode == MCLG_MODE_PLAIN || mode == 3u) {
         if (!h->plain_tuned) {
             mclg_status st = autotune_plain(h, mode, 0, h->R);
@@ -929,6 +1017,21 @@ mclg_status mclg_sync(mclg_handle h)
 }
 
 uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
+
+mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
+                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax)
+{
+    const uint32_t Jp = uint32_t(J < 0 ? -int64_t(J) : J);
+    if (!F || !dmin || !dmax || C > uint32_t(kSliceMaxC) || N < 2 || Jp > N || b > N - Jp ||
+        ((N - Jp - b) & 1u) || lambda_den < 1 || lambda_den > 256 || lambda_num > lambda_den ||
+        N > (uint32_t(1) << 20))
+        return MCLG_ERR_ARG;
+    int lo = 0, hi = 0;
+    build_slice_row(N, Jp, b, C, lambda_num, lambda_den, F, lo, hi);
+    *dmin = lo;
+    *dmax = hi;
+    return MCLG_OK;
+}
 
 mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6])
 {

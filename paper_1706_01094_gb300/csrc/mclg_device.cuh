@@ -12,6 +12,7 @@ namespace mclg {
 constexpr uint32_t kPurposeCollide = 0u;
 constexpr uint32_t kPurposeRefine = 1u;
 constexpr uint32_t kPurposeInit = 2u;
+constexpr uint32_t kPurposeSlice = 4u;
 constexpr int kChunksPerBlock = 10;  // 12-bit primary chunks in one 128-bit Philox block
 constexpr int kMaxRefine = 4;        // 16-bit refinement chunks allowed per decision
 

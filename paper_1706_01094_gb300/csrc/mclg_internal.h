@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "mclg_device.cuh"
 
@@ -13,6 +14,11 @@ constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CT
 constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
 constexpr uint32_t kPersistentVariants = 3;      // register bounds of the persistent kernel
+constexpr int kSliceMaxC = 10;                   // slice sampler: sub-collisions per step
+constexpr int kSliceRowU16 = 24;                 // primary row: 2C entries padded to 48 bytes
+constexpr int kSliceRowU64 = 20;                 // secondary row: 2C entries
+constexpr uint32_t kErrRange = 4u;               // device error bit: mass outside the tables
+constexpr uint32_t kSliceMaxN = 4096;            // largest mass the slice tables may cover
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
 
 // Device-resident description of the internal replica order.
@@ -78,6 +84,23 @@ struct StatsBuffers {
 };
 
 cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
+
+// Slice sampler (the C sub-collisions of a node drawn at once from tables).
+uint64_t slice_rows(uint32_t n_max);
+void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &primary,
+                        std::vector<uint64_t> &secondary);
+struct SliceTables {
+    uint32_t n_max;             // rows cover 2 <= N <= n_max
+    const uint32_t *rowstart;   // [(n_max + 1)^2]
+    const uint16_t *primary;    // [rows][kSliceRowU16]
+    const unsigned long long *secondary;  // [rows][kSliceRowU64]
+};
+cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
+void build_slice_row(uint32_t N, uint32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+                     uint64_t *F, int &dmin, int &dmax);
+cudaError_t launch_max_mass(const uint16_t *B, const Layout &lay, int stream, unsigned int *out,
+                            cudaStream_t s);
 uint32_t plain_variant_vec(uint32_t variant);
 size_t persistent_smem_bytes(uint32_t cap);
 cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,

@@ -18,15 +18,16 @@ from . import build as _build
 MCLG_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "occupation overflow", 5: "device wait timed out", 6: "no state set",
-          7: "sampler refinement cap reached"}
+          7: "sampler could not decide", 8: "node mass beyond the slice tables"}
 NO_STREAM = 1
 STATS = 2
 MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
+SAMPLER_SEQUENTIAL, SAMPLER_SLICE = 0, 1
 
 EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
            "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
            "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox",
-           "mclg_moments_noalloc", "mclg_tuning"]
+           "mclg_moments_noalloc", "mclg_tuning", "mclg_slice_row"]
 
 
 class MCLGError(RuntimeError):
@@ -38,7 +39,8 @@ class MCLGError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("C", ctypes.c_uint32), ("lambda_num", ctypes.c_uint32),
                 ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32),
+                ("sampler", ctypes.c_uint32), ("slice_n_max", ctypes.c_uint32)]
 
 
 _lib = None
@@ -89,6 +91,8 @@ def load() -> ctypes.CDLL:
         lib.mclg_status_str.restype = ctypes.c_char_p
         lib.mclg_philox.argtypes = [P, u64, u64, P, P]
         lib.mclg_philox.restype = st
+        lib.mclg_slice_row.argtypes = [u32, ctypes.c_int32, u32, u32, u32, u32, P, P, P]
+        lib.mclg_slice_row.restype = st
         lib.mclg_tuning.argtypes = [P, P]
         lib.mclg_tuning.restype = st
         lib.mclg_moments_noalloc.argtypes = [P, u64, P, P, P, P]
@@ -129,12 +133,13 @@ class Lattice:
     """A handle: `replicas` independent periodic D1Q3 lattices of lengths L."""
 
     def __init__(self, L, seed: int = 1, C: int = 10, lam=(1, 1), flags: int = 0,
-                 mode: int = MODE_AUTO, stream=None, first_replica: int = 0):
+                 mode: int = MODE_AUTO, stream=None, first_replica: int = 0,
+                 sampler: int = SAMPLER_SEQUENTIAL, slice_n_max: int = 0):
         self._lib = load()
         self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
         self.S = int(self.L.sum())
         self.seed = int(seed)
-        p = Params(C, lam[0], lam[1], flags, mode, first_replica)
+        p = Params(C, lam[0], lam[1], flags, mode, first_replica, sampler, slice_n_max)
         h = ctypes.c_void_p()
         _check(self._lib.mclg_create(_ptr(self.L), self.L.size, self.seed & (2**64 - 1),
                                      ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),
@@ -242,6 +247,16 @@ def moments_noalloc(n, N=None, J=None, totals=None, stream=None) -> int:
     S = int(n.shape[-1]) if len(n.shape) == 2 else int(n.shape[0]) // 3
     return int(lib.mclg_moments_noalloc(_ptr(n), S, _ptr(N), _ptr(J), _ptr(totals),
                                         _stream_ptr(stream)))
+
+
+def slice_row(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):
+    """The library's slice-sampler table row (host computation): (F, dmin, dmax)."""
+    lib = load()
+    F = np.zeros(2 * max(C, 1), dtype=np.uint64)
+    dmin, dmax = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib.mclg_slice_row(N, J, b, C, lam[0], lam[1], _ptr(F), ctypes.byref(dmin),
+                              ctypes.byref(dmax)), "mclg_slice_row")
+    return F[: dmax.value - dmin.value], int(dmin.value), int(dmax.value)
 
 
 def philox(ctr, seed: int, out=None, stream=None):

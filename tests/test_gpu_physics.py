@@ -53,14 +53,15 @@ def closed_form(pi0, n, rho, const):
     return a * pi0 / (math.exp(n / rho) * (a + pi0) - pi0)
 
 
+@pytest.mark.parametrize("sampler", [0, 1])
 @pytest.mark.parametrize("start", [(0, 300, 0), (150, 0, 150)])
-def test_pi_decay_follows_mean_field(start):
+def test_pi_decay_follows_mean_field(start, sampler):
     R, Lr, C, steps = 1000, 1000, 10, 40
     L = np.full(R, Lr, dtype=np.uint32)
     n0 = np.tile(np.array(start, dtype=np.uint16)[:, None], (1, R * Lr))
     rho = float(sum(start))
     mf = mean_field(start, C * steps)
-    with mclg.Lattice(L, seed=2024) as lat:
+    with mclg.Lattice(L, seed=2024, sampler=sampler) as lat:
         lat.set_state(n0)
         measured = [pi_moment(n0)]
         for _ in range(steps):

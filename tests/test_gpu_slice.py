@@ -1,0 +1,103 @@
+"""GPU parity of the slice sampler (the C sub-collisions of a node drawn at once
+from exact tables) against the oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_01094_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1706_01094_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1706_01094_gb300 import mclg  # noqa: E402
+
+SLICE = mclg.SAMPLER_SLICE
+
+
+def run_slice(L, seed, n0, t0, steps, **kw):
+    with mclg.Lattice(L, seed=seed, sampler=SLICE, **kw) as lat:
+        lat.set_state(n0, t=t0)
+        lat.step(steps)
+        out, t = lat.get_state()
+        assert t == t0 + steps
+    return out
+
+
+@pytest.mark.parametrize("mode", [mclg.MODE_AUTO, mclg.MODE_PLAIN, mclg.MODE_BATCHED])
+def test_slice_ragged_batch_bit_exact(mode):
+    L = [64, 1, 37, 128, 9, 1024, 5, 3, 300]
+    n0 = workloads.random_state(L, 15.0, seed=3)
+    want, err = oracle.slice_step(L, 12, n0, 6, 9)
+    assert err == 0
+    assert np.array_equal(run_slice(L, 12, n0, 6, 9, mode=mode), want)
+
+
+@pytest.mark.parametrize("C,lam", [(10, (1, 1)), (3, (1, 2)), (1, (3, 7)), (0, (1, 1)),
+                                   (10, (255, 256)), (7, (0, 1))])
+def test_slice_parameters_bit_exact(C, lam):
+    L = [50, 200, 13]
+    n0 = workloads.random_state(L, 30.0, seed=C + 1)
+    want, err = oracle.slice_step(L, 99, n0, 3, 5, C=C, lam=lam)
+    assert err == 0
+    assert np.array_equal(run_slice(L, 99, n0, 3, 5, C=C, lam=lam), want)
+
+
+def test_slice_collide_only_and_graph_replay():
+    L = [300, 41]
+    n0 = workloads.random_state(L, 25.0, seed=2)
+    want, err = oracle.slice_step(L, 8, n0, 0, 70, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    got = run_slice(L, 8, n0, 0, 70, flags=mclg.NO_STREAM)   # 2 graph replays + 6 direct
+    assert np.array_equal(got, want)
+    n1 = workloads.random_state([777], 25.0, seed=5)
+    want, err = oracle.slice_step([777], 8, n1, 11, 65)
+    assert err == 0 and np.array_equal(run_slice([777], 8, n1, 11, 65), want)
+
+
+def test_slice_range_error_and_explicit_n_max():
+    L = [16]
+    n0 = workloads.random_state(L, 10.0, seed=1)
+    n0[:, 3] = [100, 200, 100]                 # mass 400 at one node
+    with mclg.Lattice(L, seed=1, sampler=SLICE, slice_n_max=300) as lat:
+        lat.set_state(n0)
+        with pytest.raises(mclg.MCLGError):
+            lat.step(1)                        # the state's mass is beyond n_max
+    want, err = oracle.slice_step(L, 1, n0, 0, 3)
+    assert err == 0
+    assert np.array_equal(run_slice(L, 1, n0, 0, 3, slice_n_max=450), want)
+    with pytest.raises(mclg.MCLGError):
+        mclg.Lattice(L, sampler=SLICE, C=11)
+
+
+def test_slice_full_size_sampled_nodes():
+    """The 2^24-node single lattice: every sampled node's post-collision state is
+    recomputed by the oracle from the pre-step field and its own random bits."""
+    wl = workloads.single()
+    with mclg.Lattice(wl.L, seed=wl.seed, sampler=SLICE) as lat:
+        lat.init(wl.rho, wl.u)
+        lat.step(3)
+        before, t = lat.get_state()
+        lat.step(1)
+        after, _ = lat.get_state()
+    L = int(wl.L[0])
+    g = np.random.default_rng(0)
+    ys = np.concatenate([[0, 1, L - 2, L - 1], g.integers(0, L, 3000)])
+    key = (wl.seed & 0xFFFFFFFF, wl.seed >> 32)
+    for y in ys:
+        y = int(y)
+        a, b, c = (int(v) for v in before[:, y])
+        N, J = a + b + c, c - a
+        w = oracle.philox((y // 2, 0, t, 4 << 28), key)
+        lo, hi = (w[0], w[1]) if y % 2 == 0 else (w[2], w[3])
+        nb = oracle.slice_draw(N, J, b, (int(hi) << 32) | int(lo)) if N >= 2 else b
+        assert nb >= 0
+        na, nc = (N - J - nb) // 2, (N + J - nb) // 2
+        assert after[1, y] == nb
+        assert after[0, (y - 1) % L] == na      # v = -1 moved left
+        assert after[2, (y + 1) % L] == nc      # v = +1 moved right
