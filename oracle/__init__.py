@@ -63,7 +63,7 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32]
                 fn.restype = i32
-            lib.orc_slice_step.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32]
+            lib.orc_slice_step.argtypes = [P, u32, u64, u32, u32, u32, u32, P, u64, u64, u32, u32]
             lib.orc_slice_step.restype = i32
             lib.orc_slice_cdf.argtypes = [u32, ctypes.c_int32, u32, u32, u32, u32, P, P, P]
             lib.orc_slice_cdf.restype = i32
@@ -135,14 +135,15 @@ def decide(T1: int, T2: int, D: int, q0: int, refine=()) -> tuple[int, int]:
     return int(region), int(used.value)
 
 
-def _run(fn_name, L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
+def _run(fn_name, L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0,
+         extra=()):
     L = _lengths(L)
     S = int(L.sum())
     n = np.array(n, dtype=np.uint16, copy=True).reshape(3, S)
     n = np.ascontiguousarray(n)
     fn = getattr(_load(), fn_name)
     err = fn(_ptr(L), L.size, seed & (2**64 - 1), C, lam[0], lam[1], flags, _ptr(n), t0, n_steps,
-             first_replica)
+             first_replica, *extra)
     return n, int(err)
 
 
@@ -156,10 +157,16 @@ def literal_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_repli
     return _run("orc_literal_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
 
 
-def slice_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0):
+SLICE_N_MAX = 256  # the slice sampler's default table range
+
+
+def slice_step(L, seed, n, t0, n_steps, C=10, lam=(1, 1), flags=0, first_replica=0,
+               n_max=SLICE_N_MAX):
     """Time steps with the slice sampler (the C sub-collisions of a node drawn at
-    once from their exact joint law).  Returns (n, error bits)."""
-    return _run("orc_slice_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica)
+    once from their exact joint law) for nodes of mass N <= n_max; heavier nodes
+    take the sequential draws of ``step``.  Returns (n, error bits)."""
+    return _run("orc_slice_step", L, seed, n, t0, n_steps, C, lam, flags, first_replica,
+                extra=(n_max,))
 
 
 def slice_cdf(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):

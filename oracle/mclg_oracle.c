@@ -35,7 +35,8 @@
  *   orc_stats_*       pinned: hand-computed small cases; numpy cross-check.
  *   orc_slice_*       pinned: rational matrix powers of the one-sub-collision
  *                     matrix (N <= 10, and N = 150 by propagated fractions);
- *                     one-step law by chi-square; invariants.
+ *                     one-step law by chi-square; invariants; n_max below
+ *                     every mass reduces it to orc_step bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -533,6 +534,12 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
 /* [dmin, dmax) (the reachable range, CDF[dmax] = 1) U >= CDF[d] when         */
 /* Q > F[d], U < CDF[d] when Q < F[d]; Q == F[d] is reported as              */
 /* ORC_ERR_SAMPLER (probability below 2^-59 per node-step).  C <= 10.        */
+/*                                                                          */
+/* Range: the laws are tabulated for masses N <= n_max only; a node with     */
+/* N > n_max takes the sequential sampler's C decisions instead (the same    */
+/* counters and bits as orc_step gives that node).  Both are exact samplers  */
+/* of the node's C sub-collisions, so the dynamics stay exact; the bits      */
+/* depend on n_max as they depend on the seed.                              */
 /* ------------------------------------------------------------------------ */
 #define PURPOSE_SLICE 4u
 #define SLICE_MAX_C 10
@@ -703,7 +710,7 @@ int64_t orc_slice_draw(uint32_t N, int32_t J, uint32_t b, uint64_t Q, uint32_t C
 
 int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t lam_n,
                    uint32_t lam_d, uint32_t flags, uint16_t *n, uint64_t t0, uint64_t n_steps,
-                   uint32_t r0)
+                   uint32_t r0, uint32_t n_max)
 {
     if (C > SLICE_MAX_C) return 8;
     uint32_t key[2];
@@ -721,7 +728,13 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
                 uint32_t a = n[off + x], b = n[S + off + x], c = n[2 * S + off + x];
                 uint32_t N = a + b + c;
                 int32_t J = (int32_t)c - (int32_t)a;
-                if (N >= 2) {
+                if (N > n_max) {
+                    uint16_t st[3] = {(uint16_t)a, (uint16_t)b, (uint16_t)c};
+                    err |= collide_node(st, x, r0 + r, t, C, lam_n, lam_d, key);
+                    a = st[0];
+                    b = st[1];
+                    c = st[2];
+                } else if (N >= 2) {
                     uint32_t ctr[4] = {x / 2, r0 + r, t, PURPOSE_SLICE << 28}, w[4];
                     orc_philox(ctr, key, w);
                     uint32_t lo = (x % 2 == 0) ? w[0] : w[2];

@@ -111,3 +111,28 @@ def test_slice_step_invariants():
     assert err == 0 and np.array_equal(same, tiny)
     with pytest.raises(ValueError):
         oracle.slice_cdf(10, 0, 6, C=11)
+
+
+def test_nodes_beyond_n_max_take_the_sequential_draws():
+    """The range rule: with n_max below every mass the slice step is the
+    sequential step bit for bit; with n_max in the middle of the masses, the heavy
+    nodes of a collide-only step agree with the sequential step and the light
+    ones with the table draw."""
+    g = np.random.default_rng(4)
+    L = np.array([40, 17, 64], dtype=np.uint32)
+    n = g.poisson(12, size=(3, int(L.sum()))).astype(np.uint16)
+    seq, err = oracle.step(L, 21, n, 5, 6)
+    assert err == 0
+    sl, err = oracle.slice_step(L, 21, n, 5, 6, n_max=1)
+    assert err == 0 and np.array_equal(sl, seq)
+    N = n.astype(np.int64).sum(axis=0)
+    cut = int(np.median(N))
+    mixed, err = oracle.slice_step(L, 21, n, 5, 1, flags=oracle.FLAG_NO_STREAM, n_max=cut)
+    assert err == 0
+    seq1, _ = oracle.step(L, 21, n, 5, 1, flags=oracle.FLAG_NO_STREAM)
+    tab1, _ = oracle.slice_step(L, 21, n, 5, 1, flags=oracle.FLAG_NO_STREAM, n_max=4096)
+    heavy = N > cut
+    assert heavy.any() and (~heavy).any()
+    assert np.array_equal(mixed[:, heavy], seq1[:, heavy])
+    assert np.array_equal(mixed[:, ~heavy], tab1[:, ~heavy])
+    assert not np.array_equal(seq1[:, ~heavy & (N >= 2)], tab1[:, ~heavy & (N >= 2)])
