@@ -53,8 +53,14 @@ def parse():
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "uneven", "small", "fluct"])
     ap.add_argument("--u", type=float, default=0.2, help="velocity of the fluct workload")
-    ap.add_argument("--sampler", default="sequential", choices=["sequential", "slice"])
+    ap.add_argument("--sampler", default="auto", choices=["auto", "slice", "sequential"],
+                    help="slice: the C sub-collisions of a node drawn at once from exact "
+                         "cumulative-law tables; sequential: one sub-collision at a time "
+                         "(the persistent batched kernel); auto: slice for the single-lattice "
+                         "and statistics workloads, sequential for the batches")
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
+    ap.add_argument("--kernel-variant", type=int, default=None,
+                    help="fix the per-step kernel's launch variant (default: autotuned)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -68,17 +74,24 @@ def peaks():
         return {}
 
 
-def committed_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if current."""
+def committed_figure(kernel: str, workload: str, key: str = "dram_bytes_per_launch"):
+    """A figure (per-launch DRAM bytes by default) of `kernel` from the committed ncu
+    summary of that kernel on that workload, if there is one."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                return None if v in ("", "null") else float(v)
+            if line.startswith(key + ":"):
+                v = (line.split(":", 1)[1].split() or ["null"])[0]
+                return None if v == "null" else float(v)
     except OSError:
         pass
     return None
+
+
+def pick_sampler(args) -> str:
+    if args.sampler != "auto":
+        return args.sampler
+    return "slice" if args.workload in ("single", "fluct") else "sequential"
 
 
 class ClockSampler:
@@ -164,22 +177,28 @@ def sample_workload(wl, nodes: int):
     return replace(wl, L=wl.L[:k].copy(), rho=wl.rho[:m], u=wl.u[:m])
 
 
-def oracle_rate(wl, seconds: float):
+def oracle_stepper(sampler: str):
+    import oracle
+    oracle.build()
+    return oracle.slice_step if sampler == "slice" else oracle.step
+
+
+def oracle_rate(wl, seconds: float, sampler: str):
     """Time the CPU oracle (single thread, as it stands) for about `seconds` on a
     bounded sample of the workload; returns (GSUPS, sample description)."""
     import oracle
-    oracle.build()
-    probe = sample_workload(wl, 1 << 16)
+    ostep = oracle_stepper(sampler)
+    probe = sample_workload(wl, 1 << 12)
     n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
     t0 = time.perf_counter()
-    n, err = oracle.step(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
+    n, err = ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
     rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
     sw = sample_workload(wl, min(wl.nodes, max(1 << 12, int(rate * seconds / 4))))
     steps = max(1, int(rate * seconds / sw.nodes))
     n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
     assert err == 0
     t0 = time.perf_counter()
-    n, err = oracle.step(sw.L, sw.seed, n, 0, steps, C=sw.C, lam=sw.lam)
+    n, err = ostep(sw.L, sw.seed, n, 0, steps, C=sw.C, lam=sw.lam)
     dt = time.perf_counter() - t0
     sample = (f"{steps} time step(s) of a {sw.nodes}-node, {sw.replicas}-replica sample of the "
               f"workload (same profile values), {dt:.1f} s")
@@ -190,14 +209,15 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args)
     import oracle
-    oracle.build()
+    sampler_name = pick_sampler(args)
+    ostep = oracle_stepper(sampler_name)
     # size the per-step sample so that warm-up + timed steps take about two minutes
-    probe = sample_workload(wl, 1 << 16)
+    probe = sample_workload(wl, 1 << 12)
     n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
     t0 = time.perf_counter()
-    oracle.step(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
+    ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
     rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
     per_step = 120.0 / max(1, args.steps + args.warmup)
     sw = sample_workload(wl, max(1024, int(rate * per_step)))
@@ -205,11 +225,11 @@ def run_reference(args):
     assert err == 0
     t = 0
     for _ in range(args.warmup):
-        n, err = oracle.step(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
+        n, err = ostep(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
         t += 1
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        n, err = oracle.step(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
+        n, err = ostep(sw.L, sw.seed, n, t, 1, C=sw.C, lam=sw.lam)
         t += 1
     dt = time.perf_counter() - t0
     value = sw.nodes * args.steps / dt / 1e9
@@ -220,7 +240,7 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak" if wl.replicas == 1 else "strong",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": config_dict(wl, args, world),
+            "config": {**config_dict(wl, args, world), "sampler": sampler_name},
             "cpu_baseline": {"value": value, "unit": "GSUPS", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GSUPS", "h2d_bytes_per_step": 0,
@@ -255,8 +275,14 @@ def graph_launches(steps: int, per_step: int) -> int:
     return steps * per_step + groups + (1 if groups else 0)
 
 
-def count_launches(steps, wl, mode, persistent, stats_on, mclg):
+def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=False):
     """Our kernels launched by one mclg_step(steps) call, as the library issues them."""
+    if slice_sampler:
+        # per step: the table kernel and the sequential pass over heavy nodes
+        # (+ statistics: 2 passes and the count)
+        if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
+            return steps * wl.replicas * 2
+        return graph_launches(steps, 5 if stats_on else 2)
     if persistent:
         long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
         # one persistent launch per 65536 steps, plus the long replicas' batched plain steps
@@ -286,10 +312,11 @@ def run_gb300(args):
     mode = {"auto": mclg.MODE_AUTO, "plain": mclg.MODE_PLAIN, "persistent": mclg.MODE_PERSISTENT,
             "batched": mclg.MODE_BATCHED}[args.mode]
     stream = torch.cuda.Stream()
-    sampler = mclg.SAMPLER_SLICE if args.sampler == "slice" else mclg.SAMPLER_SEQUENTIAL
+    sampler_name = pick_sampler(args)
+    sampler = mclg.SAMPLER_SLICE if sampler_name == "slice" else mclg.SAMPLER_SEQUENTIAL
     lat = mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
                        first_replica=first, flags=mclg.STATS if stats_on else 0,
-                       sampler=sampler)
+                       sampler=sampler, kernel_variant=args.kernel_variant)
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 
@@ -309,7 +336,7 @@ def run_gb300(args):
     with ClockSampler(local) as clocks:
         ev0.record(stream)
         persistent = (mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)) \
-            and not stats_on
+            and not stats_on and sampler != mclg.SAMPLER_SLICE
         lat.step(args.steps)  # the library loops over the steps (CUDA graphs where it can)
         ev1.record(stream)
         ev1.synchronize()
@@ -327,7 +354,8 @@ def run_gb300(args):
     assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
     nodes_all = wl.nodes * world if wl_full.replicas == 1 else wl_full.nodes
     value = nodes_all * args.steps / (t_max / 1e3) / 1e9
-    launches = count_launches(args.steps, wl, mode, persistent, stats_on, mclg)
+    launches = count_launches(args.steps, wl, mode, persistent, stats_on, mclg,
+                              sampler == mclg.SAMPLER_SLICE)
     stats_summary = None
     if stats_on:
         st = lat.stats_read()
@@ -383,10 +411,30 @@ def run_gb300(args):
         ms_launch = ms / max(1, launches) if launches else ms
         per_launch_nodes = wl.nodes if args.mode != "plain" or wl.replicas == 1 else None
         alu_peak = INT32_LANES_PER_SM_CLK * SMS * sm_max * 1e6 / 1e9  # Gop/s
-        achieved_ops = INT_OPS_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
         achieved_gbs = BYTES_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
-        kernel = "k_step_plain" if (wl.replicas == 1 or args.mode in ("plain", "batched")) else "k_step_persistent"
-        traffic = committed_traffic(kernel, wl.name)
+        hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+               "frac": achieved_gbs / hbm_peak, "bytes_per_node_step": BYTES_PER_NODE_STEP,
+               "peak_basis": "of measured copy bandwidth"}
+        if sampler == mclg.SAMPLER_SLICE:
+            # a table lookup per node: the design bound is the state's HBM traffic
+            kernel = "k_step_slice"
+            roofline = {"bound": "hbm", **hbm, "traffic": committed_figure(kernel, wl.name),
+                        "kernel": kernel,
+                        "alu_pipe_pct_ncu": committed_figure(kernel, wl.name, "alu_pipe_pct"),
+                        "issue_active_pct_ncu": committed_figure(kernel, wl.name,
+                                                                 "issue_active_pct"),
+                        "time_basis": "whole step (table kernel + heavy-node pass) per step"}
+        else:
+            achieved_ops = INT_OPS_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
+            kernel = ("k_step_plain" if (wl.replicas == 1 or args.mode in ("plain", "batched"))
+                      else "k_step_persistent")
+            roofline = {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
+                        "unit": "Gop/s", "frac": achieved_ops / alu_peak,
+                        "traffic": committed_figure(kernel, wl.name), "kernel": kernel,
+                        "ops_per_node_step": INT_OPS_PER_NODE_STEP,
+                        "peak_basis": (f"{INT32_LANES_PER_SM_CLK} int32 lanes x {SMS} SMs x "
+                                       f"{sm_max:.0f} MHz"),
+                        "hbm": hbm}
         line = {
             "metric": METRIC, "value": value, "unit": "GSUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -394,16 +442,9 @@ def run_gb300(args):
             "scaling": "weak" if wl_full.replicas == 1 else "strong",
             "vs_baseline": None, "dtype": "u16",
             "data": "synthetic: Poisson(f^eq) initial state of the paper-shaped workload",
-            "config": {**config_dict(wl_full, args, world), "tuning": tuning},
-            "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
-                         "unit": "Gop/s", "frac": achieved_ops / alu_peak,
-                         "traffic": traffic, "kernel": kernel,
-                         "ops_per_node_step": INT_OPS_PER_NODE_STEP,
-                         "peak_basis": f"{INT32_LANES_PER_SM_CLK} int32 lanes x {SMS} SMs x {sm_max:.0f} MHz",
-                         "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                 "frac": achieved_gbs / hbm_peak,
-                                 "bytes_per_node_step": BYTES_PER_NODE_STEP,
-                                 "peak_basis": "measured copy bandwidth"}},
+            "config": {**config_dict(wl_full, args, world), "sampler": sampler_name,
+                       "tuning": tuning},
+            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "GSUPS",
                     "h2d_bytes_per_step": 6 * wl.nodes, "d2h_bytes_per_step": 6 * wl.nodes,
                     "steps": e2e_steps,
@@ -414,7 +455,7 @@ def run_gb300(args):
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
-            v, sample = oracle_rate(wl, args.cpu_seconds)
+            v, sample = oracle_rate(wl, args.cpu_seconds, sampler_name)
             line["cpu_baseline"] = {"value": v, "unit": "GSUPS", "cores": 1, "kind": "oracle",
                                     "sample": sample}
         print(json.dumps(line), flush=True)

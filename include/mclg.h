@@ -64,9 +64,8 @@ typedef enum {
     MCLG_ERR_OVERFLOW = 4, /* an occupation would leave [0, 65535]; state unspecified */
     MCLG_ERR_TIMEOUT = 5,  /* reserved: a bounded device-side wait gave up */
     MCLG_ERR_STATE = 6,    /* no state yet (call mclg_init or mclg_set_state) */
-    MCLG_ERR_SAMPLER = 7,  /* a decision stayed open (sequential: after 4 refinement chunks,
+    MCLG_ERR_SAMPLER = 7   /* a decision stayed open (sequential: after 4 refinement chunks,
                               p < 2^-70; slice: the 64-bit prefix hit a table value, p < 2^-59) */
-    MCLG_ERR_RANGE = 8     /* slice sampler: a node's mass exceeds the tables' n_max */
 } mclg_status;
 
 /* flags */
@@ -86,7 +85,8 @@ typedef enum {
  *               F[d'] = min(floor(CDF[d'] 2^64), 2^64 - 1) over the reachable
  *               offsets, Q == F[d'] reported as MCLG_ERR_SAMPLER.  Tables of F
  *               are built exactly (big integers) on the host for masses up to
- *               n_max; requires C <= 10; runs in the plain and batched modes. */
+ *               slice_n_max; heavier nodes take the SEQUENTIAL decisions.
+ *               Requires C <= 10; runs in the plain and batched modes. */
 #define MCLG_SAMPLER_SEQUENTIAL 0u
 #define MCLG_SAMPLER_SLICE 1u
 
@@ -107,13 +107,21 @@ typedef struct {
                                GPUs, each given the index of its first replica, reproduces
                                the unsplit batch bit for bit */
     uint32_t sampler;       /* MCLG_SAMPLER_* */
-    uint32_t slice_n_max;   /* SLICE: largest node mass the tables cover (<= 4096); 0 = the
-                               state's largest mass when stepping starts, plus a margin of
-                               32 + 8 sqrt(mass) */
+    uint32_t slice_n_max;   /* SLICE: the tables cover node masses N <= slice_n_max (1 ..
+                               4096; 0 = 256); a node with a larger mass takes the
+                               SEQUENTIAL sampler's C decisions (the same bits that sampler
+                               gives it).  The bits depend on slice_n_max like on the seed.
+                               Tables take about 416 (n+1)^3 / 12 bytes of device memory
+                               (0.6 GB at 256, 4.7 GB at 512); built once, at the first
+                               mclg_step, on the host cores. */
+    uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
+                                mclg_step; v + 1 = use variant v (0 <= v < 6; nodes per thread
+                                and register bound, reported by mclg_tuning).  Every variant
+                                gives the same bits; this only fixes the launch shape. */
 } mclg_params;
 
 /* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0,
- * SEQUENTIAL sampler (the paper's D1Q3 runs). */
+ * SEQUENTIAL sampler (the paper's D1Q3 runs), slice_n_max 0, kernel_variant 0. */
 void mclg_default_params(mclg_params *p);
 
 /* Create a handle for `replicas` independent periodic lattices of lengths
@@ -168,8 +176,9 @@ mclg_status mclg_sync(mclg_handle h);
 uint64_t mclg_time(mclg_handle h);
 
 /* The autotuned launch configuration of the handle (zeros before the first
- * mclg_step): cfg[0] = 100 * nodes per thread of the plain kernel + its
- * variant index (register bound), cfg[1] = threads per persistent CTA,
+ * mclg_step): cfg[0] = 100 * nodes per thread of the per-step kernel (the
+ * plain kernel, or the slice kernel with the slice sampler) + its variant
+ * index (register bound), cfg[1] = threads per persistent CTA,
  * cfg[2] = nodes per persistent work unit, cfg[3] = number of persistent work
  * units, cfg[4] = persistent register-bound variant (0, 1, 2 = 1, 2, 3 CTAs of
  * 512 threads per SM), cfg[5] = 0 (reserved). */
@@ -204,10 +213,14 @@ mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int3
 /* The slice sampler's table row for the state (N, J, b) (host computation, no
  * GPU): F[k] = min(floor(CDF[dmin + k] 2^64), 2^64 - 1) for k < dmax - dmin,
  * the exact cumulative C-step law of the rest count (F holds 2C entries);
- * *dmin, *dmax the reachable offsets.  For checking the tables against an
- * independent computation.  MCLG_ERR_ARG for C > 10 or an invalid state. */
+ * *dmin, *dmax the reachable offsets.  guide (256 bytes, or NULL) receives
+ * the row's guide entries as the device reads them: entry j is
+ * #{k : F[k] < j 2^56}, plus 0x20 when some F[k] lies in [j 2^56, (j+1) 2^56).
+ * For checking the tables against an independent computation.  MCLG_ERR_ARG
+ * for C > 10 or an invalid state. */
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
-                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax);
+                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
+                           uint8_t *guide);
 
 /* Philox4x32-10 of the library's device generator on n counters: ctr and out
  * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For

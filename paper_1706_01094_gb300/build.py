@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmclg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu", "mclg_slice_table.cu"]
+SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu", "mclg_slice_table.cu",
+           "mclg_slice_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -65,10 +65,10 @@ struct mclg_ctx {
     // slice sampler: exact cumulative C-step laws for masses up to slice.n_max
     SliceTables slice{};
     uint32_t *d_rowstart = nullptr;
-    uint16_t *d_slice_primary = nullptr;
+    unsigned long long *d_heavy_pos = nullptr;  // slice sampler: nodes beyond the tables
+    uint32_t *d_heavy_ctl = nullptr;
+    uint8_t *d_slice_guide = nullptr;
     unsigned long long *d_slice_secondary = nullptr;
-    unsigned int *d_max_mass = nullptr;
-    bool state_dirty = true;          // a new state: check its masses against the tables
     uint64_t stats_count = 0;
 };
 
@@ -101,7 +101,6 @@ mclg_status status_from_bits(uint32_t bits)
 {
     if (bits & kErrOverflow) return MCLG_ERR_OVERFLOW;
     if (bits & kErrSampler) return MCLG_ERR_SAMPLER;
-    if (bits & kErrRange) return MCLG_ERR_RANGE;
     return MCLG_OK;
 }
 
@@ -311,7 +310,9 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
     uint32_t best_variant = h->plain_variant;
     const uint16_t *in = h->d_B[h->cur];
     uint16_t *outb = h->d_B[h->cur ^ 1];
-    for (uint32_t v = 0; v < kPlainVariants; ++v) {
+    const uint32_t variants =
+        h->prm.sampler == MCLG_SAMPLER_SLICE ? kSliceVariants : kPlainVariants;
+    for (uint32_t v = 0; v < variants; ++v) {
         h->plain_variant = v;
         float ms = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {  // first launch warms up, keep the best of 3
@@ -415,35 +416,30 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
 void free_slice_tables(mclg_ctx *h)
 {
     cudaFree(h->d_rowstart);
-    cudaFree(h->d_slice_primary);
+    cudaFree(h->d_heavy_pos);
+    cudaFree(h->d_heavy_ctl);
+    h->d_heavy_pos = nullptr;
+    h->d_heavy_ctl = nullptr;
+    cudaFree(h->d_slice_guide);
     cudaFree(h->d_slice_secondary);
     h->d_rowstart = nullptr;
-    h->d_slice_primary = nullptr;
+    h->d_slice_guide = nullptr;
     h->d_slice_secondary = nullptr;
     h->slice = SliceTables{};
 }
 
-// Make sure the slice tables cover every node mass of the current state:
-// build them (exact big-integer laws, host cores) for masses up to n_max.
+// Build the slice tables (exact big-integer laws, host cores) for masses up
+// to the handle's n_max, once, and the list of heavier nodes, which take the
+// sequential draws in a second pass of each step.
 mclg_status ensure_slice_tables(mclg_ctx *h)
 {
-    MCLG_CK(launch_max_mass(h->d_B[h->cur], h->lay, streaming(h) ? 1 : 0, h->d_max_mass, h->stream));
-    unsigned int max_mass = 0;
-    MCLG_CK(cudaMemcpyAsync(&max_mass, h->d_max_mass, sizeof(max_mass), cudaMemcpyDeviceToHost,
-                            h->stream));
-    MCLG_CK(cudaStreamSynchronize(h->stream));
-    h->state_dirty = false;
-    if (h->slice.primary && max_mass <= h->slice.n_max) return MCLG_OK;
-    uint32_t n_max = h->prm.slice_n_max;
-    if (n_max == 0)
-        n_max = std::min<uint32_t>(kSliceMaxN, max_mass + 32u +
-                                                   uint32_t(8.0 * std::sqrt(double(max_mass))));
-    if (max_mass > n_max) return MCLG_ERR_RANGE;
+    if (h->slice.guide) return MCLG_OK;
+    const uint32_t n_max = h->prm.slice_n_max ? h->prm.slice_n_max : kSliceDefaultN;
     std::vector<uint32_t> rowstart;
-    std::vector<uint16_t> primary;
+    std::vector<uint8_t> guide;
     std::vector<uint64_t> secondary;
     try {
-        build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den, rowstart, primary,
+        build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den, rowstart, guide,
                            secondary);
     } catch (...) {
         return MCLG_ERR_NOMEM;
@@ -451,22 +447,27 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     MCLG_CK(cudaStreamSynchronize(h->stream));
     free_slice_tables(h);
     if (cudaMalloc(&h->d_rowstart, rowstart.size() * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_slice_primary, primary.size() * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_slice_secondary, secondary.size() * sizeof(uint64_t)) != cudaSuccess) {
+        cudaMalloc(&h->d_slice_guide, guide.size()) != cudaSuccess ||
+        cudaMalloc(&h->d_slice_secondary, secondary.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_heavy_pos, kHeavyCap * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->d_heavy_ctl, 3 * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         free_slice_tables(h);
         return MCLG_ERR_NOMEM;
     }
     MCLG_CK(cudaMemcpy(h->d_rowstart, rowstart.data(), rowstart.size() * sizeof(uint32_t),
                        cudaMemcpyHostToDevice));
-    MCLG_CK(cudaMemcpy(h->d_slice_primary, primary.data(), primary.size() * sizeof(uint16_t),
-                       cudaMemcpyHostToDevice));
+    MCLG_CK(cudaMemcpy(h->d_slice_guide, guide.data(), guide.size(), cudaMemcpyHostToDevice));
     MCLG_CK(cudaMemcpy(h->d_slice_secondary, secondary.data(), secondary.size() * sizeof(uint64_t),
                        cudaMemcpyHostToDevice));
     h->slice.n_max = n_max;
     h->slice.rowstart = h->d_rowstart;
-    h->slice.primary = h->d_slice_primary;
+    h->slice.guide = h->d_slice_guide;
     h->slice.secondary = h->d_slice_secondary;
+    MCLG_CK(cudaMemset(h->d_heavy_ctl, 0, 3 * sizeof(uint32_t)));
+    h->slice.heavy_pos = h->d_heavy_pos;
+    h->slice.heavy_ctl = h->d_heavy_ctl;
+    h->slice.heavy_cap = kHeavyCap;
     drop_graphs(h);  // captured launches hold the old table pointers
     return MCLG_OK;
 }
@@ -563,7 +564,6 @@ mclg_status upload_state(mclg_ctx *h, const uint16_t *n, uint64_t t)
     h->t = t;
     h->sticky = 0;
     h->has_state = true;
-    h->state_dirty = true;
     return MCLG_OK;
 }
 
@@ -582,6 +582,7 @@ void mclg_default_params(mclg_params *p)
     p->first_replica = 0;
     p->sampler = MCLG_SAMPLER_SEQUENTIAL;
     p->slice_n_max = 0;
+    p->kernel_variant = 0;
 }
 
 const char *mclg_status_str(mclg_status s)
@@ -595,7 +596,6 @@ const char *mclg_status_str(mclg_status s)
     case MCLG_ERR_TIMEOUT: return "device wait timed out";
     case MCLG_ERR_STATE: return "no state set";
     case MCLG_ERR_SAMPLER: return "sampler could not decide (refinement cap / table tie)";
-    case MCLG_ERR_RANGE: return "node mass beyond the slice sampler's tables";
     }
     return "unknown status";
 }
@@ -622,7 +622,6 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->d_units);
     cudaFree(h->d_unit_counter);
     cudaFree(h->d_t);
-    cudaFree(h->d_max_mass);
     free_slice_tables(h);
     cudaFree(h->lay.d_abi_off);
     cudaFree(h->lay.d_rep_off);
@@ -660,6 +659,9 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     if (S >= (uint64_t(1) << 40)) return MCLG_ERR_ARG;
     if (uint64_t(prm.first_replica) + replicas > (uint64_t(1) << 32)) return MCLG_ERR_ARG;
     if (prm.sampler > MCLG_SAMPLER_SLICE) return MCLG_ERR_ARG;
+    if (prm.kernel_variant >
+        (prm.sampler == MCLG_SAMPLER_SLICE ? kSliceVariants : kPlainVariants))
+        return MCLG_ERR_ARG;
     if (prm.sampler == MCLG_SAMPLER_SLICE &&
         (prm.C > uint32_t(kSliceMaxC) || prm.slice_n_max > kSliceMaxN))
         return MCLG_ERR_ARG;
@@ -670,6 +672,10 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     mclg_ctx *h = new (std::nothrow) mclg_ctx();
     if (!h) return MCLG_ERR_NOMEM;
     h->prm = prm;
+    if (prm.kernel_variant) {  // a fixed launch variant: no autotuning
+        h->plain_variant = prm.kernel_variant - 1u;
+        h->plain_tuned = true;
+    }
     h->seed = seed;
     h->R = replicas;
     h->L.assign(L, L + replicas);
@@ -734,7 +740,6 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         !alloc((void **)&h->d_totals, 2 * sizeof(unsigned long long)) ||
         !alloc((void **)&h->d_unit_counter, sizeof(uint32_t)) ||
         !alloc((void **)&h->d_t, sizeof(uint32_t)) ||
-        !alloc((void **)&h->d_max_mass, sizeof(unsigned int)) ||
         !alloc((void **)&h->d_stage, 3 * S * sizeof(uint16_t)) ||
         !alloc((void **)&h->lay.d_abi_off, replicas * sizeof(uint64_t)) ||
         !alloc((void **)&h->lay.d_rep_off, replicas * sizeof(uint64_t)) ||
@@ -843,11 +848,8 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     MCLG_CK(cudaSetDevice(h->device));
     const uint32_t mode = effective_mode(h);
     if (h->prm.sampler == MCLG_SAMPLER_SLICE) {
-        if (h->state_dirty) {
-            mclg_status st = ensure_slice_tables(h);
-            if (st != MCLG_OK) return st;
-        }
-        h->plain_tuned = true;  // the slice kernel has a single variant
+        mclg_status st = ensure_slice_tables(h);
+        if (st != MCLG_OK) return st;
     }
     if (mode == MCLG_MODE_PLAIN || mode == 3u) {
         if (!h->plain_tuned) {
@@ -1019,7 +1021,8 @@ mclg_status mclg_sync(mclg_handle h)
 uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
 
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
-                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax)
+                           uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
+                           uint8_t *guide)
 {
     const uint32_t Jp = uint32_t(J < 0 ? -int64_t(J) : J);
     if (!F || !dmin || !dmax || C > uint32_t(kSliceMaxC) || N < 2 || Jp > N || b > N - Jp ||
@@ -1028,6 +1031,7 @@ mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32
         return MCLG_ERR_ARG;
     int lo = 0, hi = 0;
     build_slice_row(N, Jp, b, C, lambda_num, lambda_den, F, lo, hi);
+    if (guide) build_slice_guide(F, hi - lo, guide);
     *dmin = lo;
     *dmax = hi;
     return MCLG_OK;
@@ -1038,7 +1042,9 @@ mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6])
     if (!h || !cfg) return MCLG_ERR_ARG;
     cfg[4] = h->tuned ? h->p_variant : 0u;
     cfg[5] = 0u;
-    cfg[0] = h->plain_tuned ? plain_variant_vec(h->plain_variant) * 100u + h->plain_variant : 0u;
+    const uint32_t vec = h->prm.sampler == MCLG_SAMPLER_SLICE ? slice_variant_vec(h->plain_variant)
+                                                               : plain_variant_vec(h->plain_variant);
+    cfg[0] = h->plain_tuned ? vec * 100u + h->plain_variant : 0u;
     cfg[1] = h->tuned ? h->p_threads : 0u;
     cfg[2] = h->tuned ? h->p_cap : 0u;
     cfg[3] = h->tuned ? uint32_t(h->units.size()) : 0u;

@@ -331,4 +331,43 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
     c = __float_as_uint(cf + 8388608.0f) & 0x7FFFFFu;
 }
 
+// Vector access helpers shared by the per-step kernels.
+__device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
+__device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
+
+// V consecutive uint16 values per thread: one 2-, 4-, 8- or 16-byte vector.
+template <int V> struct VecT;
+template <> struct VecT<1> { using T = uint16_t; };
+template <> struct VecT<2> { using T = uint32_t; };
+template <> struct VecT<4> { using T = uint2; };
+template <> struct VecT<8> { using T = uint4; };
+
+__device__ __forceinline__ void unpack(uint16_t v, uint32_t e[1]) { e[0] = v; }
+__device__ __forceinline__ void unpack(uint32_t v, uint32_t e[2]) { e[0] = lo16(v); e[1] = hi16(v); }
+__device__ __forceinline__ void unpack(uint2 v, uint32_t e[4])
+{
+    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
+}
+__device__ __forceinline__ void unpack(uint4 v, uint32_t e[8])
+{
+    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
+    e[4] = lo16(v.z); e[5] = hi16(v.z); e[6] = lo16(v.w); e[7] = hi16(v.w);
+}
+__device__ __forceinline__ void pack(const uint32_t e[1], uint16_t &v) { v = uint16_t(e[0]); }
+__device__ __forceinline__ void pack(const uint32_t e[2], uint32_t &v) { v = e[0] | (e[1] << 16); }
+__device__ __forceinline__ void pack(const uint32_t e[4], uint2 &v)
+{
+    v = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+}
+__device__ __forceinline__ void pack(const uint32_t e[8], uint4 &v)
+{
+    v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                   e[6] | (e[7] << 16));
+}
+
+__device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
+{
+    if (bits) atomicOr(err, bits);
+}
+
 }  // namespace mclg

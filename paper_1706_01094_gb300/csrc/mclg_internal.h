@@ -15,11 +15,13 @@ constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one per
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
 constexpr uint32_t kPersistentVariants = 3;      // register bounds of the persistent kernel
 constexpr int kSliceMaxC = 10;                   // slice sampler: sub-collisions per step
-constexpr int kSliceRowU16 = 24;                 // primary row: 2C entries padded to 48 bytes
+constexpr int kSliceBucketBits = 8;              // guide table: buckets of the top bits of Q
+constexpr int kSliceBuckets = 1 << kSliceBucketBits;
 constexpr int kSliceRowU64 = 20;                 // secondary row: 2C entries
-constexpr uint32_t kErrRange = 4u;               // device error bit: mass outside the tables
 constexpr uint32_t kSliceMaxN = 4096;            // largest mass the slice tables may cover
+constexpr uint32_t kSliceDefaultN = 256;         // slice tables' mass range unless set
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
+constexpr uint32_t kSliceVariants = 6;           // slice-kernel launch variants (see launch_slice)
 
 // Device-resident description of the internal replica order.
 struct Layout {
@@ -88,19 +90,25 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
 // Slice sampler (the C sub-collisions of a node drawn at once from tables).
 uint64_t slice_rows(uint32_t n_max);
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
-                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &primary,
+                        std::vector<uint32_t> &rowstart, std::vector<uint8_t> &guide,
                         std::vector<uint64_t> &secondary);
 struct SliceTables {
     uint32_t n_max;             // rows cover 2 <= N <= n_max
     const uint32_t *rowstart;   // [(n_max + 1)^2]
-    const uint16_t *primary;    // [rows][kSliceRowU16]
+    const uint8_t *guide;       // [rows][kSliceBuckets]: count below the bucket | 0x20 if open
     const unsigned long long *secondary;  // [rows][kSliceRowU64]
+    // nodes heavier than n_max, left for the sequential pass of the same step
+    unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
+    uint32_t *heavy_ctl;            // {count, overflow, blocks done}, zero between steps
+    uint32_t heavy_cap;
 };
+constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
+constexpr uint32_t kHeavyBlocks = 304;           // CTAs of the heavy-node pass
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
+void build_slice_guide(const uint64_t *F, int n, uint8_t *guide);
+uint32_t slice_variant_vec(uint32_t variant);
 void build_slice_row(uint32_t N, uint32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
                      uint64_t *F, int &dmin, int &dmax);
-cudaError_t launch_max_mass(const uint16_t *B, const Layout &lay, int stream, unsigned int *out,
-                            cudaStream_t s);
 uint32_t plain_variant_vec(uint32_t variant);
 size_t persistent_smem_bytes(uint32_t cap);
 cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_t threads,

@@ -22,43 +22,6 @@
 
 namespace mclg {
 
-__device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
-__device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
-
-// V consecutive uint16 values per thread: one 2-, 4-, 8- or 16-byte vector.
-template <int V> struct VecT;
-template <> struct VecT<1> { using T = uint16_t; };
-template <> struct VecT<2> { using T = uint32_t; };
-template <> struct VecT<4> { using T = uint2; };
-template <> struct VecT<8> { using T = uint4; };
-
-__device__ __forceinline__ void unpack(uint16_t v, uint32_t e[1]) { e[0] = v; }
-__device__ __forceinline__ void unpack(uint32_t v, uint32_t e[2]) { e[0] = lo16(v); e[1] = hi16(v); }
-__device__ __forceinline__ void unpack(uint2 v, uint32_t e[4])
-{
-    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
-}
-__device__ __forceinline__ void unpack(uint4 v, uint32_t e[8])
-{
-    e[0] = lo16(v.x); e[1] = hi16(v.x); e[2] = lo16(v.y); e[3] = hi16(v.y);
-    e[4] = lo16(v.z); e[5] = hi16(v.z); e[6] = lo16(v.w); e[7] = hi16(v.w);
-}
-__device__ __forceinline__ void pack(const uint32_t e[1], uint16_t &v) { v = uint16_t(e[0]); }
-__device__ __forceinline__ void pack(const uint32_t e[2], uint32_t &v) { v = e[0] | (e[1] << 16); }
-__device__ __forceinline__ void pack(const uint32_t e[4], uint2 &v)
-{
-    v = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
-}
-__device__ __forceinline__ void pack(const uint32_t e[8], uint4 &v)
-{
-    v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
-                   e[6] | (e[7] << 16));
-}
-
-__device__ __forceinline__ void flag_error(uint32_t *err, uint32_t bits)
-{
-    if (bits) atomicOr(err, bits);
-}
 
 // ---------------------------------------------------------------------------
 // Plain kernel: one thread per V consecutive nodes, any set of whole replicas
@@ -108,7 +71,8 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
         if (!(lane < 31u && x0 + V < L)) nxt = inm[off + (x0 + V < L ? x0 + V : 0u)];
         if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
     }
-    const uint32_t e = L - x0 < uint32_t(V) ? L - x0 : uint32_t(V);  // valid nodes here
+    // valid nodes here (none when the whole vector is replica padding)
+    const uint32_t e = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
     const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
 
     uint32_t err = 0;
@@ -143,134 +107,6 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
         __stcs(reinterpret_cast<T *>(p.out + p.P + node0), vo);
         pack(op, vo);
         __stcs(reinterpret_cast<T *>(p.out + 2 * p.P + node0), vo);
-        flag_error(p.err, err);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Slice-sampler kernel: the C sub-collisions of a node drawn at once.  One
-// thread per node pair (2i, 2i + 1) of a replica (pairs never straddle a
-// replica: replicas start on multiples of 8 nodes).  The pair shares one
-// Philox block; node 2i takes words (0, 1), node 2i + 1 words (2, 3) as the
-// 64-bit prefix Q of its uniform.  The node's row of the cumulative C-step law
-// on its (N, |J|) slice holds u16 prefixes G[k] of F[k] = floor(CDF 2^64) for
-// offsets d = dmin + k; the new rest count is b + 2 (dmin + #{k : Q > F[k]}).
-// Q16 = Q >> 48 decides every entry with Q16 != G[k]; rows where some entry
-// equals Q16 are finished on the u64 secondary table (Q == F[k]: sampler
-// error, probability below 2^-59).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void slice_node(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t lo,
-                                           uint32_t hi, const SliceTables &tab, uint32_t C,
-                                           uint32_t &err)
-{
-    const uint32_t N = a + b + c;
-    if (N < 2u) return;
-    if (N > tab.n_max) {
-        err |= kErrRange;
-        return;
-    }
-    const int32_t J = int32_t(c) - int32_t(a);
-    const uint32_t Jp = uint32_t(J < 0 ? -J : J);
-    const uint32_t bmin = (N - Jp) & 1u;
-    const uint32_t below = (b - bmin) >> 1, above = (N - Jp - b) >> 1;
-    const int32_t dmin = -int32_t(min(C, below));
-    const uint32_t nvalid = min(C, above) + min(C, below);  // entries dmin .. dmax - 1
-    const uint32_t row = tab.rowstart[N * (tab.n_max + 1u) + Jp] + below;
-    const uint4 *g = reinterpret_cast<const uint4 *>(tab.primary + size_t(row) * kSliceRowU16);
-    const uint32_t q16 = hi >> 16, qw = q16 | (q16 << 16);
-    uint32_t bits = 0, eq = 0;
-    const uint4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
-    const uint32_t w[10] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y};
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        bits += __popc(__vcmpgtu2(qw, w[i]));  // 16 bits per entry below Q16
-        eq |= __vcmpeq2(qw, w[i]);
-    }
-    uint32_t count = bits >> 4;
-    if (eq) {
-        // finish on the exact 64-bit values (only the row's valid entries count)
-        const uint64_t Q = (uint64_t(hi) << 32) | lo;
-        const unsigned long long *F = tab.secondary + size_t(row) * kSliceRowU64;
-        count = 0;
-        for (uint32_t k = 0; k < nvalid; ++k) {
-            const uint64_t f = F[k];
-            if (Q == f) {
-                err |= kErrSampler;
-                return;
-            }
-            count += Q > f ? 1u : 0u;
-        }
-    }
-    const uint32_t nb = uint32_t(int32_t(b) + 2 * (dmin + int32_t(count)));
-    b = nb;
-    a = uint32_t((int32_t(N) - J - int32_t(nb)) / 2);
-    c = uint32_t((int32_t(N) + J - int32_t(nb)) / 2);
-}
-
-template <bool kOne>
-__global__ void __launch_bounds__(kPlainThreads) k_step_slice(PlainArgs p, SliceTables tab)
-{
-    const bool kStream = p.stream != 0u;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t v_begin = p.g_begin * 4u, v_end = p.g_end * 4u;  // pairs
-    const uint64_t g = v_begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const bool active = g < v_end;
-    const uint64_t gv = active ? g : v_end - 1;
-    const uint64_t node0 = gv * 2u;
-
-    uint64_t off;
-    uint32_t L, rid;
-    if (kOne) {
-        off = p.one_off;
-        L = p.one_L;
-        rid = p.one_rid;
-    } else {
-        const uint32_t k = p.chunk_rep[node0 / 8u];
-        off = p.rep_off[k];
-        L = p.rep_L[k];
-        rid = p.rep_id[k];
-    }
-    const uint32_t x0 = uint32_t(node0 - off);
-
-    const uint16_t *__restrict__ inm = p.in;
-    const uint16_t *__restrict__ in0 = p.in + p.P;
-    const uint16_t *__restrict__ inp = p.in + 2 * p.P;
-    const uint32_t vm = __ldcs(reinterpret_cast<const uint32_t *>(inm + node0));
-    const uint32_t vz = __ldcs(reinterpret_cast<const uint32_t *>(in0 + node0));
-    const uint32_t vp = __ldcs(reinterpret_cast<const uint32_t *>(inp + node0));
-    uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, lo16(vm), 1);
-    uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, hi16(vp), 1);
-    if (kStream) {
-        if (!(lane < 31u && x0 + 2u < L)) nxt = inm[off + (x0 + 2u < L ? x0 + 2u : 0u)];
-        if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
-    }
-    const bool v1 = x0 + 1u < L;  // the pair's second node exists
-    uint32_t a0, b0, c0, a1, b1, c1;
-    if (kStream) {
-        a0 = v1 ? hi16(vm) : nxt;
-        c0 = prv;
-        a1 = nxt;
-        c1 = lo16(vp);
-    } else {
-        a0 = lo16(vm);
-        c0 = lo16(vp);
-        a1 = hi16(vm);
-        c1 = hi16(vp);
-    }
-    b0 = lo16(vz);
-    b1 = hi16(vz);
-    if (!v1) a1 = b1 = c1 = 0u;
-
-    const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
-    uint32_t w0 = x0 >> 1, w1 = rid + p.r0, w2 = t, w3 = kPurposeSlice << 28;
-    philox4x32_10(w0, w1, w2, w3, p.rk);
-    uint32_t err = 0;
-    slice_node(a0, b0, c0, w0, w1, tab, p.C, err);
-    slice_node(a1, b1, c1, w2, w3, tab, p.C, err);
-    if (active) {
-        __stcs(reinterpret_cast<uint32_t *>(p.out + node0), a0 | (a1 << 16));
-        __stcs(reinterpret_cast<uint32_t *>(p.out + p.P + node0), b0 | (b1 << 16));
-        __stcs(reinterpret_cast<uint32_t *>(p.out + 2 * p.P + node0), c0 | (c1 << 16));
         flag_error(p.err, err);
     }
 }
@@ -605,30 +441,6 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
     }
 }
 
-// Largest node mass N of the canonical field (for sizing the slice tables).
-__global__ void k_max_mass(const uint16_t *__restrict__ B, uint64_t P, const uint64_t *__restrict__ abi_off,
-                           const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
-                           const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
-                           const uint32_t *__restrict__ rep_id, int stream, unsigned int *out)
-{
-    const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    uint32_t m = 0;
-    if (g < chunks) {
-        const ChunkInfo c = chunk_info(g, abi_off, rep_off, rep_L, chunk_rep, rep_id);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t x = c.x0 + uint32_t(j);
-            if (x < c.L) {
-                const uint32_t xr = stream ? (x + 1u == c.L ? 0u : x + 1u) : x;
-                const uint32_t xl = stream ? (x == 0u ? c.L - 1u : x - 1u) : x;
-                m = max(m, uint32_t(B[c.base + xr]) + B[P + c.base + x] + B[2 * P + c.base + xl]);
-            }
-        }
-    }
-    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, d));
-    if ((threadIdx.x & 31u) == 0) atomicMax(out, m);
-}
-
 __global__ void k_count_add(unsigned long long *count, uint32_t R) { *count += R; }
 
 __global__ void k_set_time(uint32_t *t_dev, uint32_t value) { *t_dev = value; }
@@ -774,30 +586,6 @@ cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, 
     k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, R, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_count_add<<<1, 1, 0, s>>>(st.count, R);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s)
-{
-    const uint64_t chunks = p.g_end - p.g_begin;
-    if (chunks == 0) return cudaSuccess;
-    const uint64_t pairs = chunks * 4u;
-    const dim3 grid(uint32_t((pairs + kPlainThreads - 1) / kPlainThreads));
-    if (one) k_step_slice<true><<<grid, kPlainThreads, 0, s>>>(p, tab);
-    else k_step_slice<false><<<grid, kPlainThreads, 0, s>>>(p, tab);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_max_mass(const uint16_t *B, const Layout &lay, int stream, unsigned int *out,
-                            cudaStream_t s)
-{
-    const uint64_t chunks = lay.P / 8u;
-    const uint32_t th = 256;
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    k_max_mass<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
-        B, lay.P, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks, lay.d_rep_id,
-        stream, out);
     return cudaGetLastError();
 }
 

@@ -3,9 +3,12 @@
 // count after C sub-collisions (Sec. III, Sec. III.A: the C-th power of the
 // one-sub-collision matrix), as exact fixed-point values
 //     F[d] = min(floor(CDF[d] 2^64), 2^64 - 1),   d = dmin .. dmax - 1,
-// stored per row re-based at dmin: a u64 secondary table and a u16 primary
-// table (the top 16 bits) that the kernel reads first.  The law is symmetric
-// under J -> -J (it depends on a c and b only), so only J >= 0 is stored.
+// stored per row re-based at dmin (the u64 secondary table), and a guide
+// table that the kernel reads first: for each of the 2^8 buckets of the top
+// bits of a 64-bit uniform Q, the number of entries below the bucket's start,
+// with bit 0x20 set when an entry lies inside the bucket (then Q is compared
+// with the u64 entries from that count on).  The law is symmetric under
+// J -> -J (it depends on a c and b only), so only J >= 0 is stored.
 //
 // Exact arithmetic: numerators over D^C with D = 8 N^2 lam_d, in fixed-size
 // unsigned big integers of 64-bit limbs.
@@ -214,15 +217,28 @@ uint64_t slice_rows(uint32_t n_max)
     return rows;
 }
 
+// Guide row of one law: entry j = #{k : F[k] < j 2^56}, plus 0x20 when some
+// F[k] lies in [j 2^56, (j + 1) 2^56).
+void build_slice_guide(const uint64_t *F, int n, uint8_t *guide)
+{
+    constexpr int kShift = 64 - kSliceBucketBits;
+    int k = 0;
+    for (int j = 0; j < kSliceBuckets; ++j) {
+        while (k < n && (F[k] >> kShift) < uint64_t(j)) ++k;
+        const bool open = k < n && (F[k] >> kShift) == uint64_t(j);
+        guide[j] = uint8_t(k | (open ? 0x20 : 0));
+    }
+}
+
 // Fills rowstart[N * (n_max + 1) + J] (first row of the (N, J) slice),
-// primary[row * kSliceRowU16 + k] and secondary[row * kSliceRowU64 + k].
+// guide[row * kSliceBuckets + j] and secondary[row * kSliceRowU64 + k].
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
-                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &primary,
+                        std::vector<uint32_t> &rowstart, std::vector<uint8_t> &guide,
                         std::vector<uint64_t> &secondary)
 {
     const uint64_t rows = slice_rows(n_max);
     rowstart.assign(size_t(n_max + 1) * (n_max + 1), 0u);
-    primary.assign(rows * kSliceRowU16, 0xFFFFu);
+    guide.assign(rows * kSliceBuckets, 0u);
     secondary.assign(rows * kSliceRowU64, UINT64_MAX);
     uint64_t r = 0;
     for (uint32_t N = 0; N <= n_max; ++N)
@@ -247,10 +263,8 @@ void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam
                         int dmin, dmax;
                         build_row(uint32_t(N), J, b, sp, F, dmin, dmax);
                         const uint64_t row = first + (b - bmin) / 2;
-                        for (int i = 0; i < dmax - dmin; ++i) {
-                            secondary[row * kSliceRowU64 + i] = F[i];
-                            primary[row * kSliceRowU16 + i] = uint16_t(F[i] >> 48);
-                        }
+                        for (int i = 0; i < dmax - dmin; ++i) secondary[row * kSliceRowU64 + i] = F[i];
+                        build_slice_guide(F, dmax - dmin, &guide[row * kSliceBuckets]);
                     }
                 }
         });

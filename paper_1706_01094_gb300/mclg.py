@@ -18,7 +18,7 @@ from . import build as _build
 MCLG_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "occupation overflow", 5: "device wait timed out", 6: "no state set",
-          7: "sampler could not decide", 8: "node mass beyond the slice tables"}
+          7: "sampler could not decide"}
 NO_STREAM = 1
 STATS = 2
 MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
     _fields_ = [("C", ctypes.c_uint32), ("lambda_num", ctypes.c_uint32),
                 ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32),
-                ("sampler", ctypes.c_uint32), ("slice_n_max", ctypes.c_uint32)]
+                ("sampler", ctypes.c_uint32), ("slice_n_max", ctypes.c_uint32),
+                ("kernel_variant", ctypes.c_uint32)]
 
 
 _lib = None
@@ -91,7 +92,7 @@ def load() -> ctypes.CDLL:
         lib.mclg_status_str.restype = ctypes.c_char_p
         lib.mclg_philox.argtypes = [P, u64, u64, P, P]
         lib.mclg_philox.restype = st
-        lib.mclg_slice_row.argtypes = [u32, ctypes.c_int32, u32, u32, u32, u32, P, P, P]
+        lib.mclg_slice_row.argtypes = [u32, ctypes.c_int32, u32, u32, u32, u32, P, P, P, P]
         lib.mclg_slice_row.restype = st
         lib.mclg_tuning.argtypes = [P, P]
         lib.mclg_tuning.restype = st
@@ -134,12 +135,14 @@ class Lattice:
 
     def __init__(self, L, seed: int = 1, C: int = 10, lam=(1, 1), flags: int = 0,
                  mode: int = MODE_AUTO, stream=None, first_replica: int = 0,
-                 sampler: int = SAMPLER_SEQUENTIAL, slice_n_max: int = 0):
+                 sampler: int = SAMPLER_SEQUENTIAL, slice_n_max: int = 0,
+                 kernel_variant=None):
         self._lib = load()
         self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
         self.S = int(self.L.sum())
         self.seed = int(seed)
-        p = Params(C, lam[0], lam[1], flags, mode, first_replica, sampler, slice_n_max)
+        kv = 0 if kernel_variant is None else int(kernel_variant) + 1  # None: autotune
+        p = Params(C, lam[0], lam[1], flags, mode, first_replica, sampler, slice_n_max, kv)
         h = ctypes.c_void_p()
         _check(self._lib.mclg_create(_ptr(self.L), self.L.size, self.seed & (2**64 - 1),
                                      ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),
@@ -249,14 +252,17 @@ def moments_noalloc(n, N=None, J=None, totals=None, stream=None) -> int:
                                         _stream_ptr(stream)))
 
 
-def slice_row(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):
-    """The library's slice-sampler table row (host computation): (F, dmin, dmax)."""
+def slice_row(N: int, J: int, b: int, C: int = 10, lam=(1, 1), guide: bool = False):
+    """The library's slice-sampler table row (host computation): (F, dmin, dmax),
+    and the row's 256 guide entries as a fourth item when ``guide``."""
     lib = load()
     F = np.zeros(2 * max(C, 1), dtype=np.uint64)
+    G = np.zeros(256, dtype=np.uint8)
     dmin, dmax = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(lib.mclg_slice_row(N, J, b, C, lam[0], lam[1], _ptr(F), ctypes.byref(dmin),
-                              ctypes.byref(dmax)), "mclg_slice_row")
-    return F[: dmax.value - dmin.value], int(dmin.value), int(dmax.value)
+                              ctypes.byref(dmax), _ptr(G) if guide else None), "mclg_slice_row")
+    out = (F[: dmax.value - dmin.value], int(dmin.value), int(dmax.value))
+    return out + (G,) if guide else out
 
 
 def philox(ctr, seed: int, out=None, stream=None):

@@ -389,3 +389,18 @@ def test_statistics_ragged_lengths_exact(Lc, R):
     assert np.array_equal(st["s1"], ref.s1)
     assert np.array_equal(st["s2"], ref.s2)
     assert np.array_equal(st["snb"], ref.snb)
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_every_plain_launch_variant_bit_exact(variant):
+    """Each launch shape of the plain kernel (1 or 2 nodes per thread, register
+    bounds) gives the oracle's bits, per replica and batched, including replicas
+    whose padding fills whole vectors."""
+    L = [8, 3, 100, 1, 517, 64, 6]
+    n0 = workloads.random_state(L, 40.0, seed=variant)
+    want, err = oracle.step(L, 5, n0, 2, 4)
+    assert err == 0
+    for mode in (mclg.MODE_BATCHED, mclg.MODE_PLAIN):
+        assert np.array_equal(run_gpu(L, 5, n0, 2, 4, mode=mode, kernel_variant=variant), want)
+    with pytest.raises(mclg.MCLGError):
+        mclg.Lattice(L, kernel_variant=6)  # six variants: 0 .. 5

@@ -60,19 +60,26 @@ def test_slice_collide_only_and_graph_replay():
     assert err == 0 and np.array_equal(run_slice([777], 8, n1, 11, 65), want)
 
 
-def test_slice_range_error_and_explicit_n_max():
-    L = [16]
+@pytest.mark.parametrize("variant", [0, 2, 5])
+def test_nodes_beyond_n_max_take_sequential_draws(variant):
+    """Masses above the tables' range collide with the sequential sampler's draws,
+    node by node as the oracle does; with n_max = 1 the whole step equals the
+    sequential sampler's."""
+    L = [16, 333, 40]
     n0 = workloads.random_state(L, 10.0, seed=1)
     n0[:, 3] = [100, 200, 100]                 # mass 400 at one node
-    with mclg.Lattice(L, seed=1, sampler=SLICE, slice_n_max=300) as lat:
-        lat.set_state(n0)
-        with pytest.raises(mclg.MCLGError):
-            lat.step(1)                        # the state's mass is beyond n_max
-    want, err = oracle.slice_step(L, 1, n0, 0, 3)
+    for n_max in (20, 300, 450):
+        want, err = oracle.slice_step(L, 1, n0, 0, 6, n_max=n_max)
+        assert err == 0
+        got = run_slice(L, 1, n0, 0, 6, slice_n_max=n_max, kernel_variant=variant)
+        assert np.array_equal(got, want), n_max
+    seq, err = oracle.step(L, 1, n0, 0, 6)
     assert err == 0
-    assert np.array_equal(run_slice(L, 1, n0, 0, 3, slice_n_max=450), want)
+    assert np.array_equal(run_slice(L, 1, n0, 0, 6, slice_n_max=1, kernel_variant=variant), seq)
     with pytest.raises(mclg.MCLGError):
         mclg.Lattice(L, sampler=SLICE, C=11)
+    with pytest.raises(mclg.MCLGError):
+        mclg.Lattice(L, sampler=SLICE, slice_n_max=4097)
 
 
 def test_slice_full_size_sampled_nodes():
@@ -101,3 +108,21 @@ def test_slice_full_size_sampled_nodes():
         assert after[1, y] == nb
         assert after[0, (y - 1) % L] == na      # v = -1 moved left
         assert after[2, (y + 1) % L] == nc      # v = +1 moved right
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_slice_every_launch_variant_bit_exact(variant):
+    """Each launch shape of the slice kernel (2, 4 or 8 nodes per thread, register
+    bounds) gives the oracle's bits, on ragged replicas whose ends fall inside a
+    thread's vector and on one long lattice."""
+    L = [8, 3, 100, 1, 517, 64, 6]
+    n0 = workloads.random_state(L, 40.0, seed=variant)
+    want, err = oracle.slice_step(L, 5, n0, 2, 4)
+    assert err == 0
+    for mode in (mclg.MODE_BATCHED, mclg.MODE_PLAIN):
+        got = run_slice(L, 5, n0, 2, 4, mode=mode, kernel_variant=variant)
+        assert np.array_equal(got, want), mode
+    n1 = workloads.random_state([4099], 90.0, seed=7)
+    want, err = oracle.slice_step([4099], 6, n1, 1, 3)
+    assert err == 0
+    assert np.array_equal(run_slice([4099], 6, n1, 1, 3, kernel_variant=variant), want)

@@ -43,3 +43,26 @@ def test_rows_are_cumulative_and_symmetric(lib):
         lib.slice_row(10, 0, 5)        # parity of b does not match the slice
     with pytest.raises(lib.MCLGError):
         lib.slice_row(10, 0, 4, C=11)  # the slice sampler draws at most 10 at once
+
+
+def test_guide_rows_count_entries_below_each_bucket(lib):
+    """Guide entry j of a row = #{k : F[k] < j 2^56} (the oracle's F), with bit
+    0x20 exactly when an entry lies inside bucket j; every bucket without that
+    bit then decides #{k : Q > F[k]}, hence the new rest count, for all Q in it."""
+    rnd = random.Random(11)
+    for _ in range(150):
+        N = rnd.randint(2, 300)
+        J = rnd.randint(-N, N)
+        b = rnd.randrange((N - abs(J)) & 1, N - abs(J) + 1, 2)
+        C = rnd.choice([1, 3, 10])
+        lam = rnd.choice([(1, 1), (2, 5), (0, 1)])
+        F, dmin, dmax, G = lib.slice_row(N, J, b, C, lam, guide=True)
+        Fo, omin, omax = oracle.slice_cdf(N, J, b, C, lam)
+        Fo = [int(Fo[d + C]) for d in range(omin, omax)]
+        for j in range(256):
+            below = sum(1 for f in Fo if f < j << 56)
+            inside = any(j << 56 <= f < (j + 1) << 56 for f in Fo)
+            assert int(G[j]) == below | (0x20 if inside else 0), (N, J, b, C, lam, j)
+            if not inside:  # the count is the same for the bucket's first and last Q
+                for Q in (j << 56, ((j + 1) << 56) - 1):
+                    assert oracle.slice_draw(N, J, b, Q, C, lam) == b + 2 * (omin + below)
