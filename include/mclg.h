@@ -213,14 +213,16 @@ mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int3
 /* The slice sampler's table row for the state (N, J, b) (host computation, no
  * GPU): F[k] = min(floor(CDF[dmin + k] 2^64), 2^64 - 1) for k < dmax - dmin,
  * the exact cumulative C-step law of the rest count (F holds 2C entries);
- * *dmin, *dmax the reachable offsets.  guide (256 bytes, or NULL) receives
- * the row's guide entries as the device reads them: entry j is
- * #{k : F[k] < j 2^56}, plus 0x20 when some F[k] lies in [j 2^56, (j+1) 2^56).
+ * *dmin, *dmax the reachable offsets.  guide (256 uint16, or NULL) receives
+ * the row's guide entries as the device reads them; for bucket j =
+ * [j 2^56, (j+1) 2^56): bits 0-4 #{k : F[k] < j 2^56}, bits 5-6
+ * min(#{k : F[k] in bucket j}, 3), bits 8-15 bits 55..48 of that F[k] when
+ * it is the only one in the bucket (else 0).
  * For checking the tables against an independent computation.  MCLG_ERR_ARG
  * for C > 10 or an invalid state. */
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
-                           uint8_t *guide);
+                           uint16_t *guide);
 
 /* Philox4x32-10 of the library's device generator on n counters: ctr and out
  * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For

@@ -67,7 +67,7 @@ struct mclg_ctx {
     uint32_t *d_rowstart = nullptr;
     unsigned long long *d_heavy_pos = nullptr;  // slice sampler: nodes beyond the tables
     uint32_t *d_heavy_ctl = nullptr;
-    uint8_t *d_slice_guide = nullptr;
+    uint16_t *d_slice_guide = nullptr;
     unsigned long long *d_slice_secondary = nullptr;
     uint64_t stats_count = 0;
 };
@@ -436,7 +436,7 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     if (h->slice.guide) return MCLG_OK;
     const uint32_t n_max = h->prm.slice_n_max ? h->prm.slice_n_max : kSliceDefaultN;
     std::vector<uint32_t> rowstart;
-    std::vector<uint8_t> guide;
+    std::vector<uint16_t> guide;
     std::vector<uint64_t> secondary;
     try {
         build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den, rowstart, guide,
@@ -447,7 +447,7 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     MCLG_CK(cudaStreamSynchronize(h->stream));
     free_slice_tables(h);
     if (cudaMalloc(&h->d_rowstart, rowstart.size() * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_slice_guide, guide.size()) != cudaSuccess ||
+        cudaMalloc(&h->d_slice_guide, guide.size() * sizeof(uint16_t)) != cudaSuccess ||
         cudaMalloc(&h->d_slice_secondary, secondary.size() * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_heavy_pos, kHeavyCap * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&h->d_heavy_ctl, 3 * sizeof(uint32_t)) != cudaSuccess) {
@@ -457,7 +457,8 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     }
     MCLG_CK(cudaMemcpy(h->d_rowstart, rowstart.data(), rowstart.size() * sizeof(uint32_t),
                        cudaMemcpyHostToDevice));
-    MCLG_CK(cudaMemcpy(h->d_slice_guide, guide.data(), guide.size(), cudaMemcpyHostToDevice));
+    MCLG_CK(cudaMemcpy(h->d_slice_guide, guide.data(), guide.size() * sizeof(uint16_t),
+                       cudaMemcpyHostToDevice));
     MCLG_CK(cudaMemcpy(h->d_slice_secondary, secondary.data(), secondary.size() * sizeof(uint64_t),
                        cudaMemcpyHostToDevice));
     h->slice.n_max = n_max;
@@ -1022,7 +1023,7 @@ uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
 
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
-                           uint8_t *guide)
+                           uint16_t *guide)
 {
     const uint32_t Jp = uint32_t(J < 0 ? -int64_t(J) : J);
     if (!F || !dmin || !dmax || C > uint32_t(kSliceMaxC) || N < 2 || Jp > N || b > N - Jp ||

@@ -90,12 +90,15 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
 // Slice sampler (the C sub-collisions of a node drawn at once from tables).
 uint64_t slice_rows(uint32_t n_max);
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
-                        std::vector<uint32_t> &rowstart, std::vector<uint8_t> &guide,
+                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
                         std::vector<uint64_t> &secondary);
 struct SliceTables {
     uint32_t n_max;             // rows cover 2 <= N <= n_max
     const uint32_t *rowstart;   // [(n_max + 1)^2]
-    const uint8_t *guide;       // [rows][kSliceBuckets]: count below the bucket | 0x20 if open
+    // [rows][kSliceBuckets]: bits 0-4 the number of entries below the bucket,
+    // bits 5-6 min(entries inside it, 3), bits 8-15 the next 8 bits (56..48)
+    // of the entry when it is the only one inside
+    const uint16_t *guide;
     const unsigned long long *secondary;  // [rows][kSliceRowU64]
     // nodes heavier than n_max, left for the sequential pass of the same step
     unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
@@ -105,7 +108,7 @@ struct SliceTables {
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
 constexpr uint32_t kHeavyBlocks = 304;           // CTAs of the heavy-node pass
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
-void build_slice_guide(const uint64_t *F, int n, uint8_t *guide);
+void build_slice_guide(const uint64_t *F, int n, uint16_t *guide);
 uint32_t slice_variant_vec(uint32_t variant);
 void build_slice_row(uint32_t N, uint32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
                      uint64_t *F, int &dmin, int &dmax);

@@ -14,7 +14,10 @@
 // block: node 2i takes words (0, 1), node 2i + 1 words (2, 3) as Q.  The
 // row's guide entry for the top 8 bits of Q gives the count directly unless
 // an F[k] falls inside Q's bucket (about 3% of nodes near equilibrium); then
-// Q is compared with the row's u64 entries from the guide's count on.
+// the entry also holds that F[k]'s next 8 bits, which decide Q against it
+// unless Q has the same 16 top bits (or several entries share the bucket,
+// mostly in the tails): then Q is compared with the row's u64 entries from
+// the guide's count on (below 1% of nodes near equilibrium).
 //
 // A node heavier than the tables' n_max takes the sequential sampler's C
 // decisions (the bits that sampler gives it) in a second, small pass of the
@@ -46,8 +49,12 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
     const uint32_t e =
         __ldg(tab.guide + (uint64_t(row) << kSliceBucketBits) + (hi >> (32 - kSliceBucketBits)));
     uint32_t count = e & 0x1Fu;
-    if (e & 0x20u) {
-        // an entry lies in Q's bucket: finish on the exact 64-bit values
+    const uint32_t inside = (e >> 5) & 3u;  // entries in Q's bucket (3: three or more)
+    const uint32_t qn = (hi >> (24 - kSliceBucketBits)) & 0xFFu, fn = e >> 8;  // Q bits 55..48
+    if (inside == 1u && qn != fn) {
+        count += qn > fn ? 1u : 0u;  // the next 8 bits decide Q against that entry
+    } else if (inside != 0u) {
+        // finish on the exact 64-bit values
         const uint32_t above = (N - Jp - b) >> 1;
         const uint32_t nvalid = min(C, above) + min(C, below);  // entries dmin .. dmax - 1
         const uint64_t Q = (uint64_t(hi) << 32) | lo;
@@ -182,6 +189,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_step_heavy(PlainArgs p, Slice
     const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
     const uint64_t first = p.g_begin * 8u, end = p.g_end * 8u;
     const uint64_t n = scan ? end - first : min(count, tab.heavy_cap);
+    if (n == 0 && !scan) return;  // nothing listed: the list is already clear
     uint32_t err = 0;
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += uint64_t(gridDim.x) * blockDim.x) {

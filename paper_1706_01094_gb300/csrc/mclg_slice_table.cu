@@ -6,8 +6,9 @@
 // stored per row re-based at dmin (the u64 secondary table), and a guide
 // table that the kernel reads first: for each of the 2^8 buckets of the top
 // bits of a 64-bit uniform Q, the number of entries below the bucket's start,
-// with bit 0x20 set when an entry lies inside the bucket (then Q is compared
-// with the u64 entries from that count on).  The law is symmetric under
+// how many lie inside it and, when exactly one does, its next 8 bits, which
+// decide Q against it unless Q shares them too; the rest is decided on the
+// u64 entries.  The law is symmetric under
 // J -> -J (it depends on a c and b only), so only J >= 0 is stored.
 //
 // Exact arithmetic: numerators over D^C with D = 8 N^2 lam_d, in fixed-size
@@ -217,23 +218,26 @@ uint64_t slice_rows(uint32_t n_max)
     return rows;
 }
 
-// Guide row of one law: entry j = #{k : F[k] < j 2^56}, plus 0x20 when some
-// F[k] lies in [j 2^56, (j + 1) 2^56).
-void build_slice_guide(const uint64_t *F, int n, uint8_t *guide)
+// Guide row of one law, for each bucket j = [j 2^56, (j + 1) 2^56):
+// below = #{k : F[k] < j 2^56}, inside = #{k : F[k] in bucket j};
+// entry = below | min(inside, 3) << 5 | (inside == 1 ? bits 55..48 of that F : 0) << 8.
+void build_slice_guide(const uint64_t *F, int n, uint16_t *guide)
 {
     constexpr int kShift = 64 - kSliceBucketBits;
     int k = 0;
     for (int j = 0; j < kSliceBuckets; ++j) {
         while (k < n && (F[k] >> kShift) < uint64_t(j)) ++k;
-        const bool open = k < n && (F[k] >> kShift) == uint64_t(j);
-        guide[j] = uint8_t(k | (open ? 0x20 : 0));
+        int inside = 0;
+        while (k + inside < n && (F[k + inside] >> kShift) == uint64_t(j)) ++inside;
+        const uint32_t next8 = inside == 1 ? uint32_t(F[k] >> (kShift - 8)) & 0xFFu : 0u;
+        guide[j] = uint16_t(uint32_t(k) | uint32_t(inside < 3 ? inside : 3) << 5 | next8 << 8);
     }
 }
 
 // Fills rowstart[N * (n_max + 1) + J] (first row of the (N, J) slice),
 // guide[row * kSliceBuckets + j] and secondary[row * kSliceRowU64 + k].
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
-                        std::vector<uint32_t> &rowstart, std::vector<uint8_t> &guide,
+                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
                         std::vector<uint64_t> &secondary)
 {
     const uint64_t rows = slice_rows(n_max);

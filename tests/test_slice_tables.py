@@ -46,9 +46,11 @@ def test_rows_are_cumulative_and_symmetric(lib):
 
 
 def test_guide_rows_count_entries_below_each_bucket(lib):
-    """Guide entry j of a row = #{k : F[k] < j 2^56} (the oracle's F), with bit
-    0x20 exactly when an entry lies inside bucket j; every bucket without that
-    bit then decides #{k : Q > F[k]}, hence the new rest count, for all Q in it."""
+    """Guide entry j of a row (bucket [j 2^56, (j+1) 2^56)) holds #{k : F[k] below
+    the bucket} (the oracle's F), min(#inside, 3) and, for a single entry inside,
+    its bits 55..48; a bucket with no entry decides #{k : Q > F[k]}, hence the new
+    rest count, for all Q in it, and one with a single entry decides every Q whose
+    bits 55..48 differ from the entry's."""
     rnd = random.Random(11)
     for _ in range(150):
         N = rnd.randint(2, 300)
@@ -61,8 +63,14 @@ def test_guide_rows_count_entries_below_each_bucket(lib):
         Fo = [int(Fo[d + C]) for d in range(omin, omax)]
         for j in range(256):
             below = sum(1 for f in Fo if f < j << 56)
-            inside = any(j << 56 <= f < (j + 1) << 56 for f in Fo)
-            assert int(G[j]) == below | (0x20 if inside else 0), (N, J, b, C, lam, j)
-            if not inside:  # the count is the same for the bucket's first and last Q
+            ins = [f for f in Fo if j << 56 <= f < (j + 1) << 56]
+            next8 = (ins[0] >> 48) & 0xFF if len(ins) == 1 else 0
+            assert int(G[j]) == below | min(len(ins), 3) << 5 | next8 << 8, (N, J, b, C, lam, j)
+            if not ins:  # the count is the same for the bucket's first and last Q
                 for Q in (j << 56, ((j + 1) << 56) - 1):
                     assert oracle.slice_draw(N, J, b, Q, C, lam) == b + 2 * (omin + below)
+            elif len(ins) == 1 and 0 < next8 < 255:  # Q's bits 55..48 decide against it
+                lo_q = (j << 56) | ((next8 - 1) << 48) | ((1 << 48) - 1)
+                hi_q = (j << 56) | ((next8 + 1) << 48)
+                assert oracle.slice_draw(N, J, b, lo_q, C, lam) == b + 2 * (omin + below)
+                assert oracle.slice_draw(N, J, b, hi_q, C, lam) == b + 2 * (omin + below + 1)
