@@ -69,6 +69,8 @@ def _load():
             lib.orc_slice_cdf.restype = i32
             lib.orc_slice_draw.argtypes = [u32, ctypes.c_int32, u32, u64, u32, u32, u32]
             lib.orc_slice_draw.restype = ctypes.c_int64
+            lib.orc_slice_q.argtypes = [u32, u32, u32, P]
+            lib.orc_slice_q.restype = u64
             lib.orc_moments.argtypes = [P, u32, P, P, P, P]
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
             lib.orc_exact_cov.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, u64]
@@ -179,6 +181,12 @@ def slice_cdf(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):
     if rc != 0:
         raise ValueError("C too large for the slice sampler")
     return F, int(dmin.value), int(dmax.value)
+
+
+def slice_q(x: int, r: int, t: int, seed: int) -> int:
+    """The slice sampler's 64-bit uniform prefix Q of node x of replica r at time t."""
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    return int(_load().orc_slice_q(x, r, t, _ptr(key)))
 
 
 def slice_draw(N: int, J: int, b: int, Q: int, C: int = 10, lam=(1, 1)) -> int:

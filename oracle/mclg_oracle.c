@@ -528,12 +528,9 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
 /* integers.  The node then takes b' = b + 2 d with d the first offset whose */
 /* cumulative probability CDF[d] exceeds a uniform U.                        */
 /*                                                                          */
-/* Contract: U's first 64 bits are Q = h 2^48 + m 2^32 + w0.  h is 16-bit    */
-/* chunk x mod 8 (bits [16 (x mod 8), +16)) of Philox block                 */
-/* (x/8, r, t, PURPOSE_SLICE << 28), shared by the 8 nodes x/8 covers; m and  */
-/* w0 are the low 16 bits of word 1 and word 0 of block                     */
-/* (x, r, t, PURPOSE_SLICE_LOW << 28).  F[d] = min(floor(CDF[d] 2^64),       */
-/* 2^64 - 1); for d in                                                      */
+/* Contract: U's first 64 bits are Q = w1 2^32 + w0 with (w0, w1) = words    */
+/* (0, 1) of Philox block (x/2, r, t, PURPOSE_SLICE << 28) for even x and    */
+/* words (2, 3) for odd x; F[d] = min(floor(CDF[d] 2^64), 2^64 - 1); for d in */
 /* [dmin, dmax) (the reachable range, CDF[dmax] = 1) U >= CDF[d] when         */
 /* Q > F[d], U < CDF[d] when Q < F[d]; Q == F[d] is reported as              */
 /* ORC_ERR_SAMPLER (probability below 2^-59 per node-step).  C <= 10.        */
@@ -545,7 +542,6 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
 /* depend on n_max as they depend on the seed.                              */
 /* ------------------------------------------------------------------------ */
 #define PURPOSE_SLICE 4u
-#define PURPOSE_SLICE_LOW 5u
 #define SLICE_MAX_C 10
 #define BN_LIMBS 20 /* 640-bit unsigned integers in 32-bit limbs */
 
@@ -697,6 +693,17 @@ int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n,
     return 0;
 }
 
+/* The 64-bit uniform prefix Q of node x of replica r at time t (the
+ * contract above). */
+uint64_t orc_slice_q(uint32_t x, uint32_t r, uint32_t t, const uint32_t key[2])
+{
+    uint32_t ctr[4] = {x / 2, r, t, PURPOSE_SLICE << 28}, w[4];
+    orc_philox(ctr, key, w);
+    uint32_t lo = (x % 2 == 0) ? w[0] : w[2];
+    uint32_t hi = (x % 2 == 0) ? w[1] : w[3];
+    return ((uint64_t)hi << 32) | lo;
+}
+
 /* The new rest count of one node, or -1 for an undecided prefix. */
 int64_t orc_slice_draw(uint32_t N, int32_t J, uint32_t b, uint64_t Q, uint32_t C,
                           uint32_t lam_n, uint32_t lam_d)
@@ -739,12 +746,7 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
                     b = st[1];
                     c = st[2];
                 } else if (N >= 2) {
-                    uint32_t ctr[4] = {x / 8, r0 + r, t, PURPOSE_SLICE << 28}, w[4];
-                    orc_philox(ctr, key, w);
-                    uint64_t h = (w[(x % 8) / 2] >> (16 * (x % 2))) & 0xFFFFu;
-                    uint32_t ctr2[4] = {x, r0 + r, t, PURPOSE_SLICE_LOW << 28}, w2[4];
-                    orc_philox(ctr2, key, w2);
-                    uint64_t Q = (h << 48) | ((uint64_t)(w2[1] & 0xFFFFu) << 32) | w2[0];
+                    uint64_t Q = orc_slice_q(x, r0 + r, t, key);
                     int64_t nb = orc_slice_draw(N, J, b, Q, C, lam_n, lam_d);
                     if (nb < 0) {
                         err |= ORC_ERR_SAMPLER;

@@ -95,14 +95,12 @@ def test_slice_full_size_sampled_nodes():
     L = int(wl.L[0])
     g = np.random.default_rng(0)
     ys = np.concatenate([[0, 1, L - 2, L - 1], g.integers(0, L, 3000)])
-    key = (wl.seed & 0xFFFFFFFF, wl.seed >> 32)
     for y in ys:
         y = int(y)
         a, b, c = (int(v) for v in before[:, y])
         N, J = a + b + c, c - a
-        w = oracle.philox((y // 2, 0, t, 4 << 28), key)
-        lo, hi = (w[0], w[1]) if y % 2 == 0 else (w[2], w[3])
-        nb = oracle.slice_draw(N, J, b, (int(hi) << 32) | int(lo)) if N >= 2 else b
+        assert N <= oracle.SLICE_N_MAX                # every node on the tables here
+        nb = oracle.slice_draw(N, J, b, oracle.slice_q(y, 0, t, wl.seed)) if N >= 2 else b
         assert nb >= 0
         na, nc = (N - J - nb) // 2, (N + J - nb) // 2
         assert after[1, y] == nb
@@ -114,7 +112,7 @@ def test_slice_full_size_sampled_nodes():
 def test_slice_every_launch_variant_bit_exact(variant):
     """Each launch shape of the slice kernel (2, 4 or 8 nodes per thread, register
     bounds) gives the oracle's bits, on ragged replicas whose ends fall inside a
-    thread's vector and on one long lattice."""
+    thread's vector, on one long lattice, and without streaming."""
     L = [8, 3, 100, 1, 517, 64, 6]
     n0 = workloads.random_state(L, 40.0, seed=variant)
     want, err = oracle.slice_step(L, 5, n0, 2, 4)
@@ -126,3 +124,9 @@ def test_slice_every_launch_variant_bit_exact(variant):
     want, err = oracle.slice_step([4099], 6, n1, 1, 3)
     assert err == 0
     assert np.array_equal(run_slice([4099], 6, n1, 1, 3, kernel_variant=variant), want)
+    with pytest.raises(mclg.MCLGError):
+        mclg.Lattice(L, sampler=SLICE, kernel_variant=6)  # six variants: 0 .. 5
+    want, err = oracle.slice_step(L, 5, n0, 2, 4, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    got = run_slice(L, 5, n0, 2, 4, flags=mclg.NO_STREAM, kernel_variant=variant)
+    assert np.array_equal(got, want)

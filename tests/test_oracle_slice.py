@@ -136,3 +136,18 @@ def test_nodes_beyond_n_max_take_the_sequential_draws():
     assert np.array_equal(mixed[:, heavy], seq1[:, heavy])
     assert np.array_equal(mixed[:, ~heavy], tab1[:, ~heavy])
     assert not np.array_equal(seq1[:, ~heavy & (N >= 2)], tab1[:, ~heavy & (N >= 2)])
+
+
+def test_slice_uniform_bits_are_uniform_and_independent():
+    """Q (two words of a Philox block per node, two nodes per block) behaves as
+    uniform bits: each byte of Q is uniform over 256 values, neighbouring
+    nodes' top bytes are uncorrelated, and no two nodes share a prefix."""
+    qs = np.array([oracle.slice_q(x, 3, 7, 12345) for x in range(16384)], dtype=np.uint64)
+    for shift in (56, 48, 40, 0):
+        counts = np.bincount(((qs >> np.uint64(shift)) & np.uint64(0xFF)).astype(np.int64),
+                             minlength=256)
+        chi2 = ((counts - 64.0) ** 2 / 64.0).sum()
+        assert stats.chi2.sf(chi2, 255) > 1e-4, shift
+    top = (qs >> np.uint64(56)).astype(np.float64)
+    assert abs(np.corrcoef(top[:-1], top[1:])[0, 1]) < 0.04
+    assert len(set(int(q) for q in qs)) == len(qs)
