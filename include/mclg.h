@@ -111,8 +111,8 @@ typedef struct {
                                4096; 0 = 256); a node with a larger mass takes the
                                SEQUENTIAL sampler's C decisions (the same bits that sampler
                                gives it).  The bits depend on slice_n_max like on the seed.
-                               Tables take about 416 (n+1)^3 / 12 bytes of device memory
-                               (0.6 GB at 256, 4.7 GB at 512); built once, at the first
+                               Tables take about 672 (n+1)^3 / 12 bytes of device memory
+                               (1.0 GB at 256, 7.6 GB at 512); built once, at the first
                                mclg_step, on the host cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
                                 mclg_step; v + 1 = use variant v (0 <= v < 6; nodes per thread
