@@ -30,6 +30,7 @@ _lib = None
 ERR_OVERFLOW = 1
 ERR_SAMPLER = 2
 FLAG_NO_STREAM = 1
+FLAG_GALILEAN = 4
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +71,8 @@ def _load():
             lib.orc_slice_draw.argtypes = [u32, ctypes.c_int32, u32, u64, u32, u32, u32]
             lib.orc_slice_draw.restype = ctypes.c_int64
             lib.orc_slice_q.argtypes = [u32, u32, u32, P]
+            lib.orc_galilean_q.argtypes = [u32, ctypes.c_int32, u32, u32]
+            lib.orc_galilean_q.restype = u32
             lib.orc_slice_q.restype = u64
             lib.orc_moments.argtypes = [P, u32, P, P, P, P]
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
@@ -181,6 +184,11 @@ def slice_cdf(N: int, J: int, b: int, C: int = 10, lam=(1, 1)):
     if rc != 0:
         raise ValueError("C too large for the slice sampler")
     return F, int(dmin.value), int(dmax.value)
+
+
+def galilean_q(N: int, J: int, lam=(1, 1)) -> int:
+    """Numerator q of the node's Galilean-invariant collision rate q / 256."""
+    return int(_load().orc_galilean_q(N, J, lam[0], lam[1]))
 
 
 def slice_q(x: int, r: int, t: int, seed: int) -> int:

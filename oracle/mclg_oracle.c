@@ -33,6 +33,7 @@
  *   orc_init          pinned: sample mean/variance against Eq. D1Q3equil.
  *   orc_moments       pinned: hand-computed small cases.
  *   orc_stats_*       pinned: hand-computed small cases; numpy cross-check.
+ *   orc_galilean_q    pinned: 50-digit decimal evaluation of lt / sqrt(1 + 3 u^2).
  *   orc_slice_*       pinned: rational matrix powers of the one-sub-collision
  *                     matrix (N <= 10, and N = 150 by propagated fractions);
  *                     one-step law by chi-square; invariants; n_max below
@@ -47,6 +48,7 @@
 #define ORC_ERR_SAMPLER 2u  /* decision still open after the refinement cap */
 
 #define ORC_FLAG_NO_STREAM 1u /* collide only: local equilibration (Sec. IV.A, Fig. decay) */
+#define ORC_FLAG_GALILEAN 4u  /* per-node lambda = lambda~ / sqrt(1 + 3 u^2) (end of Sec. IV.A) */
 
 /* Random-stream purposes (top 4 bits of the fourth Philox counter word). */
 #define PURPOSE_COLLIDE 0u
@@ -334,6 +336,37 @@ static void stream(const uint32_t *L, uint32_t R, uint64_t S, const uint16_t *po
     }
 }
 
+/* Galilean-invariant collision rate (end of Sec. IV.A): lambda = lt / sqrt(1 + 3 u^2)
+ * with the node's velocity u = J / N and lt = lt_n / lt_d, quantised down to q / 256:
+ * the largest integer q with  q lt_d sqrt(N^2 + 3 J^2) <= 256 lt_n N,  i.e.
+ * q^2 lt_d^2 (N^2 + 3 J^2) <= (256 lt_n N)^2, decided in 128-bit integers after a
+ * floating-point first guess. */
+uint32_t orc_galilean_q(uint32_t N, int32_t J, uint32_t lt_n, uint32_t lt_d)
+{
+    if (N == 0) return 0;
+    unsigned __int128 R = (unsigned __int128)N * N + (unsigned __int128)3 * ((int64_t)J * J);
+    unsigned __int128 rhs = (unsigned __int128)(256ull * lt_n * N) * (256ull * lt_n * N);
+    double guess = 256.0 * lt_n * N / (lt_d * sqrt((double)R));
+    uint64_t q = guess >= 256.0 ? 256 : (uint64_t)guess;
+    while (q > 0 && (unsigned __int128)(q * q * lt_d * lt_d) * R > rhs) q--;
+    while (q < 256 && (unsigned __int128)((q + 1) * (q + 1) * lt_d * lt_d) * R <= rhs) q++;
+    return (uint32_t)q;
+}
+
+/* The node's collision rate as (numerator, denominator): the handle's lambda, or the
+ * Galilean-invariant one when flags ask for it. */
+static void node_lambda(uint32_t flags, uint32_t N, int32_t J, uint32_t lam_n, uint32_t lam_d,
+                        uint32_t *ln, uint32_t *ld)
+{
+    if (flags & ORC_FLAG_GALILEAN) {
+        *ln = orc_galilean_q(N, J, lam_n, lam_d);
+        *ld = 256;
+    } else {
+        *ln = lam_n;
+        *ld = lam_d;
+    }
+}
+
 /* n_steps time steps from time t0.  n holds the pre-collision occupations
  * n_i(x, t0) on entry and n_i(x, t0 + n_steps) on return.  Collision at
  * (replica r, local node x, time t) draws from Philox counters (x, r0 + r,
@@ -356,7 +389,10 @@ int orc_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t 
         for (uint32_t r = 0; r < R; r++) {
             for (uint32_t x = 0; x < L[r]; x++) {
                 uint16_t st[3] = {n[0 * S + off + x], n[1 * S + off + x], n[2 * S + off + x]};
-                err |= collide_node(st, x, r0 + r, t, C, lam_n, lam_d, key);
+                uint32_t ln, ld;
+                node_lambda(flags, (uint32_t)st[0] + st[1] + st[2], (int32_t)st[2] - (int32_t)st[0],
+                            lam_n, lam_d, &ln, &ld);
+                err |= collide_node(st, x, r0 + r, t, C, ln, ld, key);
                 for (int i = 0; i < 3; i++) post[i * S + off + x] = st[i];
             }
             off += L[r];
@@ -424,6 +460,8 @@ int orc_literal_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, u
                 int64_t cnt[3] = {n[off + x], n[S + off + x], n[2 * S + off + x]};
                 word_stream ws = {x, r0 + r, t, 0, 4, {0, 0, 0, 0}, key};
                 uint32_t N = (uint32_t)(cnt[0] + cnt[1] + cnt[2]);
+                uint32_t ln, ld;
+                node_lambda(flags, N, (int32_t)(cnt[2] - cnt[0]), lam_n, lam_d, &ln, &ld);
                 for (uint32_t k = 0; k < C && N >= 2; k++) {
                     uint32_t r1 = 1 + uniform_below(&ws, N);
                     uint32_t r2 = 1 + uniform_below(&ws, N);
@@ -432,13 +470,13 @@ int orc_literal_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, u
                     if (r1 == r2) continue; /* one particle cannot collide with itself */
                     if ((s1 == 0 && s2 == 2) || (s1 == 2 && s2 == 0)) {
                         /* P_{-1 1 -> 0 0} = P_{1 -1 -> 0 0} = lambda */
-                        if (uniform_below(&ws, lam_d) < lam_n) {
+                        if (uniform_below(&ws, ld) < ln) {
                             cnt[0] -= 1; cnt[1] += 2; cnt[2] -= 1;
                         }
                     } else if (s1 == 1 && s2 == 1) {
                         /* P_{00 -> -1 1} = P_{00 -> 1 -1} = lambda / 16 */
-                        uint32_t v = uniform_below(&ws, 16 * lam_d);
-                        if (v < 2 * lam_n) {
+                        uint32_t v = uniform_below(&ws, 16 * ld);
+                        if (v < 2 * ln) {
                             cnt[0] += 1; cnt[1] -= 2; cnt[2] += 1;
                         }
                     }
@@ -739,15 +777,17 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
                 uint32_t a = n[off + x], b = n[S + off + x], c = n[2 * S + off + x];
                 uint32_t N = a + b + c;
                 int32_t J = (int32_t)c - (int32_t)a;
+                uint32_t ln, ld;
+                node_lambda(flags, N, J, lam_n, lam_d, &ln, &ld);
                 if (N > n_max) {
                     uint16_t st[3] = {(uint16_t)a, (uint16_t)b, (uint16_t)c};
-                    err |= collide_node(st, x, r0 + r, t, C, lam_n, lam_d, key);
+                    err |= collide_node(st, x, r0 + r, t, C, ln, ld, key);
                     a = st[0];
                     b = st[1];
                     c = st[2];
                 } else if (N >= 2) {
                     uint64_t Q = orc_slice_q(x, r0 + r, t, key);
-                    int64_t nb = orc_slice_draw(N, J, b, Q, C, lam_n, lam_d);
+                    int64_t nb = orc_slice_draw(N, J, b, Q, C, ln, ld);
                     if (nb < 0) {
                         err |= ORC_ERR_SAMPLER;
                     } else {

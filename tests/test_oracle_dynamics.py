@@ -133,3 +133,42 @@ def test_poisson_statistics_preserved():
         corr = cov / np.sqrt(f[i] * f[j])
         target = 1.0 if i == j else 0.0
         assert abs(corr - target) < 0.06, (i, j, corr)
+
+
+def test_galilean_rate_is_lambda_over_sqrt_1_plus_3u2_rounded_down():
+    """q / 256 <= lt / sqrt(1 + 3 u^2) < (q + 1) / 256 with u = J / N (end of
+    Sec. IV.A), checked in 50-digit decimal arithmetic, including exact ties."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    g = np.random.default_rng(9)
+    cases = [(100, 0, (1, 1)), (5, 5, (1, 1)), (100, 30, (1, 1)), (7, -3, (3, 7)), (60000, 17, (255, 256))]
+    cases += [(int(N), int(g.integers(-N, N + 1)), (int(a), int(b)))
+              for N, (a, b) in zip(g.integers(2, 200000, 400),
+                                   [(g.integers(0, 9), 8)] * 200 + [(1, 1)] * 200)]
+    for N, J, (ln, ld) in cases:
+        q = oracle.galilean_q(N, J, (ln, ld))
+        lam = Decimal(ln) / Decimal(ld) / (1 + 3 * (Decimal(J) / Decimal(N)) ** 2).sqrt()
+        assert Decimal(q) / 256 <= lam < Decimal(q + 1) / 256, (N, J, ln, ld, q)
+
+
+@pytest.mark.parametrize("stepper", ["step", "slice_step"])
+def test_galilean_rate_at_rest_nodes_is_the_constant_rate(stepper):
+    """With J = 0 at every node (kept by collisions without streaming) the
+    Galilean-invariant rate is lambda~ itself, so the step equals the plain step
+    at lambda = lambda~ bit for bit (the exact decisions compare with the same
+    rational thresholds)."""
+    fn = getattr(oracle, stepper)
+    L = np.array([64, 33], dtype=np.uint32)
+    g = np.random.default_rng(2)
+    side = g.poisson(6, int(L.sum())).astype(np.uint16)
+    n = np.stack([side, g.poisson(20, int(L.sum())).astype(np.uint16), side])
+    flags = oracle.FLAG_NO_STREAM
+    want, err = fn(L, 4, n, 0, 5, lam=(1, 2), flags=flags)
+    assert err == 0
+    got, err = fn(L, 4, n, 0, 5, lam=(1, 2), flags=flags | oracle.FLAG_GALILEAN)
+    assert err == 0 and np.array_equal(got, want)
+    moving = n.copy()
+    moving[2] += 3                               # J = 3 at every node: a slower rate
+    a, _ = fn(L, 4, moving, 0, 5, lam=(1, 2), flags=flags)
+    b, _ = fn(L, 4, moving, 0, 5, lam=(1, 2), flags=flags | oracle.FLAG_GALILEAN)
+    assert not np.array_equal(a, b)
