@@ -71,6 +71,10 @@ typedef enum {
 /* flags */
 #define MCLG_NO_STREAM 1u /* collide only, no streaming (the "without streaming" runs of Fig. decay) */
 #define MCLG_STATS 2u     /* accumulate ensemble statistics after every step (Sec. V) */
+#define MCLG_GALILEAN 4u  /* Galilean-invariant collision rate (end of Sec. IV.A): each node
+                             collides with lambda(N, J) = q / 256, q the largest integer with
+                             q / 256 <= lambda / sqrt(1 + 3 u^2), u = J / N, lambda the
+                             handle's lambda_num / lambda_den; both samplers */
 
 /* samplers: two exact ways to draw the C sub-collisions of a node, with
  * different uses of the random bits (each is bit-exact to its own oracle):

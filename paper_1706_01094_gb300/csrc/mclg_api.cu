@@ -159,6 +159,7 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.err = h->d_err;
     a.variant = h->plain_variant;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.galilean = (h->prm.flags & MCLG_GALILEAN) ? 1u : 0u;
     a.r0 = h->prm.first_replica;
     a.t_dev = nullptr;
     a.rk = make_round_keys(h->seed);
@@ -219,6 +220,7 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.k1 = uint32_t(h->seed >> 32);
     a.err = h->d_err;
     a.stream = (h->prm.flags & MCLG_NO_STREAM) ? 0u : 1u;
+    a.galilean = (h->prm.flags & MCLG_GALILEAN) ? 1u : 0u;
     a.r0 = h->prm.first_replica;
     a.rk = make_round_keys(h->seed);
     a.unit_counter = h->d_unit_counter;
@@ -439,7 +441,8 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     std::vector<uint16_t> guide;
     std::vector<uint64_t> secondary;
     try {
-        build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den, rowstart, guide,
+        build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den,
+                           (h->prm.flags & MCLG_GALILEAN) != 0u, rowstart, guide,
                            secondary);
     } catch (...) {
         return MCLG_ERR_NOMEM;
@@ -651,7 +654,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     mclg_default_params(&prm);
     if (p) prm = *p;
     if (prm.lambda_den < 1 || prm.lambda_den > 256 || prm.lambda_num > prm.lambda_den) return MCLG_ERR_ARG;
-    if (prm.mode > MCLG_MODE_BATCHED || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS))) return MCLG_ERR_ARG;
+    if (prm.mode > MCLG_MODE_BATCHED || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS | MCLG_GALILEAN))) return MCLG_ERR_ARG;
     uint64_t S = 0;
     for (uint32_t r = 0; r < replicas; ++r) {
         if (L[r] == 0 || L[r] > (uint32_t(1) << 31)) return MCLG_ERR_ARG;

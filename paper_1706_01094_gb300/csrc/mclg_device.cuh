@@ -331,6 +331,35 @@ __device__ __forceinline__ void collide_node(uint32_t &a, uint32_t &b, uint32_t 
     c = __float_as_uint(cf + 8388608.0f) & 0x7FFFFFu;
 }
 
+// Galilean-invariant collision rate (end of Sec. IV.A): lambda = lt / sqrt(1 + 3 u^2)
+// with the node's velocity u = J / N and lt = lt_n / lt_d, quantised down to q / 256:
+// the largest q with q^2 lt_d^2 (N^2 + 3 J^2) <= (256 lt_n N)^2.  A single-precision
+// first guess is settled by exact 128-bit comparisons (host and device).
+__host__ __device__ inline uint32_t galilean_q(uint32_t N, int32_t J, uint32_t lt_n, uint32_t lt_d)
+{
+    if (N == 0u) return 0u;
+    const uint64_t R = uint64_t(N) * N + 3ull * uint64_t(int64_t(J) * J);
+    const uint64_t s = 256ull * lt_n * N;
+    const unsigned __int128 rhs = (unsigned __int128)s * s;
+    const float guess = 256.0f * float(lt_n) * float(N) / (float(lt_d) * sqrtf(float(R)));
+    uint64_t q = guess >= 256.0f ? 256u : uint64_t(guess);
+    while (q > 0u && (unsigned __int128)(q * q * lt_d * lt_d) * R > rhs) --q;
+    while (q < 256u && (unsigned __int128)((q + 1u) * (q + 1u) * lt_d * lt_d) * R <= rhs) ++q;
+    return uint32_t(q);
+}
+
+// The handle's rate, or the node's Galilean-invariant one, as (numerator, denominator).
+__device__ __forceinline__ void node_rate(bool galilean, uint32_t a, uint32_t b, uint32_t c,
+                                          uint32_t lam_n, uint32_t lam_d, uint32_t &ln, uint32_t &ld)
+{
+    ln = lam_n;
+    ld = lam_d;
+    if (galilean) {
+        ln = galilean_q(a + b + c, int32_t(c) - int32_t(a), lam_n, lam_d);
+        ld = 256u;
+    }
+}
+
 // Vector access helpers shared by the per-step kernels.
 __device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xFFFFu; }
 __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }

@@ -48,6 +48,7 @@ struct PlainArgs {
     uint32_t *err;
     uint32_t variant;  // plain-kernel variant (nodes per thread, register bound)
     uint32_t stream;   // 1: pull-stream before colliding, 0: collide only
+    uint32_t galilean; // 1: per-node rate lambda / sqrt(1 + 3 u^2) (galilean_q)
     uint32_t r0;       // random-stream index of replica id 0
     const uint32_t *t_dev;  // if set, the time step is *t_dev + t (graph replays)
     RoundKeys rk;      // Philox round keys of the seed
@@ -74,6 +75,7 @@ struct PersistentArgs {
     uint32_t t0, n_steps, C, lam_n, lam_d, k0, k1;
     uint32_t *err;
     uint32_t stream;  // 1: pull-stream before colliding, 0: collide only
+    uint32_t galilean; // 1: per-node rate lambda / sqrt(1 + 3 u^2) (galilean_q)
     uint32_t r0;      // random-stream index of replica id 0
     RoundKeys rk;     // Philox round keys of the seed
 };
@@ -89,7 +91,7 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
 
 // Slice sampler (the C sub-collisions of a node drawn at once from tables).
 uint64_t slice_rows(uint32_t n_max);
-void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d, bool galilean,
                         std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
                         std::vector<uint64_t> &secondary);
 struct SliceTables {

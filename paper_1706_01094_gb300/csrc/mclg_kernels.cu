@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
         }
         if (uint32_t(j) < e) {
             const NodeKey nk{x0 + uint32_t(j), rid + p.r0, t, p.k0, p.k1};
-            collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
+            uint32_t ln, ld;
+            node_rate(p.galilean != 0u, a, b, c, p.lam_n, p.lam_d, ln, ld);
+            collide_node(a, b, c, nk, p.rk, p.C, ln, ld, err);
         } else {
             a = b = c = 0u;
         }
@@ -186,8 +188,11 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_pers
                 const uint32_t rid = s_rid[lo] + p.r0;
                 const NodeKey nk0{x, rid, t, p.k0, p.k1};
                 const NodeKey nk1{x + 1u, rid, t, p.k0, p.k1};
-                collide_node(a0, b0, c0, nk0, p.rk, p.C, p.lam_n, p.lam_d, err);
-                collide_node(a1, b1, c1, nk1, p.rk, p.C, p.lam_n, p.lam_d, err);
+                uint32_t ln, ld;
+                node_rate(p.galilean != 0u, a0, b0, c0, p.lam_n, p.lam_d, ln, ld);
+                collide_node(a0, b0, c0, nk0, p.rk, p.C, ln, ld, err);
+                node_rate(p.galilean != 0u, a1, b1, c1, p.lam_n, p.lam_d, ln, ld);
+                collide_node(a1, b1, c1, nk1, p.rk, p.C, ln, ld, err);
                 *reinterpret_cast<uint32_t *>(om + i) = a0 | (a1 << 16);
                 *reinterpret_cast<uint32_t *>(oz + i) = b0 | (b1 << 16);
                 *reinterpret_cast<uint32_t *>(op + i) = c0 | (c1 << 16);

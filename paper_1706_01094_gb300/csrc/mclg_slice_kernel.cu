@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(kPlainThreads) k_step_heavy(PlainArgs p, Slice
         uint32_t a = p.out[pos], b = p.out[p.P + pos], c = p.out[2 * p.P + pos];
         if (x >= L || a + b + c <= tab.n_max) continue;  // padding, or a table node (scan)
         const NodeKey nk{x, rid + p.r0, t, p.k0, p.k1};
-        collide_node(a, b, c, nk, p.rk, p.C, p.lam_n, p.lam_d, err);
+        uint32_t ln, ld;
+        node_rate(p.galilean != 0u, a, b, c, p.lam_n, p.lam_d, ln, ld);
+        collide_node(a, b, c, nk, p.rk, p.C, ln, ld, err);
         p.out[pos] = uint16_t(a);
         p.out[p.P + pos] = uint16_t(b);
         p.out[2 * p.P + pos] = uint16_t(c);

@@ -20,6 +20,7 @@
 #include <thread>
 #include <vector>
 
+#include "mclg_device.cuh"
 #include "mclg_internal.h"
 
 namespace mclg {
@@ -236,7 +237,7 @@ void build_slice_guide(const uint64_t *F, int n, uint16_t *guide)
 
 // Fills rowstart[N * (n_max + 1) + J] (first row of the (N, J) slice),
 // guide[row * kSliceBuckets + j] and secondary[row * kSliceRowU64 + k].
-void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d, bool galilean,
                         std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
                         std::vector<uint64_t> &secondary)
 {
@@ -250,7 +251,6 @@ void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam
             rowstart[size_t(N) * (n_max + 1) + J] = uint32_t(r);
             r += (N - J) / 2 + 1;
         }
-    const SliceParams sp{C, lam_n, lam_d};
     // spread the slices over the host cores, larger N first
     unsigned nth = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
     std::vector<std::thread> pool;
@@ -262,6 +262,10 @@ void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam
                 for (uint32_t J = 0; J <= uint32_t(N); ++J, ++k) {
                     if (k % nth != w) continue;
                     const uint32_t first = rowstart[size_t(N) * (n_max + 1) + J];
+                    // the slice's rate: the handle's, or the Galilean-invariant one of (N, J)
+                    const SliceParams sp = galilean
+                        ? SliceParams{C, galilean_q(uint32_t(N), int32_t(J), lam_n, lam_d), 256u}
+                        : SliceParams{C, lam_n, lam_d};
                     const uint32_t bmin = uint32_t(N - J) & 1u;
                     for (uint32_t b = bmin; b <= uint32_t(N) - J; b += 2) {
                         int dmin, dmax;

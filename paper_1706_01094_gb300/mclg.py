@@ -21,6 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime e
           7: "sampler could not decide"}
 NO_STREAM = 1
 STATS = 2
+GALILEAN = 4
 MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
 SAMPLER_SEQUENTIAL, SAMPLER_SLICE = 0, 1
 

@@ -404,3 +404,17 @@ def test_every_plain_launch_variant_bit_exact(variant):
         assert np.array_equal(run_gpu(L, 5, n0, 2, 4, mode=mode, kernel_variant=variant), want)
     with pytest.raises(mclg.MCLGError):
         mclg.Lattice(L, kernel_variant=6)  # six variants: 0 .. 5
+
+
+@pytest.mark.parametrize("mode", [mclg.MODE_PLAIN, mclg.MODE_BATCHED, mclg.MODE_PERSISTENT])
+def test_galilean_rate_bit_exact(mode):
+    """The Galilean-invariant collision rate (end of Sec. IV.A), node by node as the
+    oracle computes it, in every mode of the sequential sampler."""
+    L = [64, 37, 300, 9]
+    g = np.random.default_rng(13)
+    S = sum(L)
+    n0 = np.stack([g.poisson(3, S), g.poisson(12, S), g.poisson(9, S)]).astype(np.uint16)
+    want, err = oracle.step(L, 21, n0, 3, 12, lam=(3, 4), flags=oracle.FLAG_GALILEAN)
+    assert err == 0
+    got = run_gpu(L, 21, n0, 3, 12, lam=(3, 4), flags=mclg.GALILEAN, mode=mode)
+    assert np.array_equal(got, want)

@@ -133,3 +133,44 @@ def test_even_rest_particles_keep_parity_and_restricted_poisson():
     assert emp[1::2].sum() == 0.0
     sel = p > 1e-3
     assert np.all(np.abs(emp[sel] - p[sel]) < 0.02 * p[sel] + 3e-4), (emp[:12], p[:12])
+
+
+def relaxation_rate(state, flags, sampler, R=1000, Lr=100, steps=40):
+    """Collide-only decay rate per step of the ensemble-mean rest count towards its
+    equilibrium, from identical nodes (N and J stay fixed at every node)."""
+    L = np.full(R, Lr, dtype=np.uint32)
+    n0 = np.tile(np.array(state, dtype=np.uint16)[:, None], (1, R * Lr))
+    means = []
+    with mclg.Lattice(L, seed=31, flags=mclg.NO_STREAM | flags, sampler=sampler) as lat:
+        lat.set_state(n0)
+        means.append(float(n0[1].mean()))
+        for _ in range(steps):
+            lat.step(1)
+            means.append(float(lat.get_state()[0][1].astype(np.float64).mean()))
+        lat.step(400)
+        tail = []
+        for _ in range(20):
+            lat.step(5)
+            tail.append(float(lat.get_state()[0][1].astype(np.float64).mean()))
+    dev = np.array(means) - np.mean(tail)
+    k = np.arange(len(dev))
+    use = np.abs(dev) > 4.0
+    slope = np.polyfit(k[use], np.log(np.abs(dev[use])), 1)[0]
+    return -slope
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_galilean_rate_makes_relaxation_independent_of_u(sampler):
+    """Eq. D1Q3relax: the pi mode relaxes with rate C lambda sqrt(1 + 3u^2) / rho per
+    step near equilibrium.  With lambda = lambda~ / sqrt(1 + 3u^2) (end of Sec. IV.A)
+    the rate at u = 0.3 equals the one at rest; with a constant lambda it is
+    sqrt(1.27) = 1.127 times larger."""
+    at_rest = (40, 220, 40)      # N = 300, J = 0, b 20 above equilibrium
+    moving = (8, 194, 98)        # N = 300, J = 90 (u = 0.3), b ~ 20 above equilibrium
+    r0 = relaxation_rate(at_rest, mclg.GALILEAN, sampler)
+    r1 = relaxation_rate(moving, mclg.GALILEAN, sampler)
+    c0 = relaxation_rate(at_rest, 0, sampler)
+    c1 = relaxation_rate(moving, 0, sampler)
+    assert abs(r1 / r0 - 1.0) < 0.04, (r0, r1)
+    assert abs(c1 / c0 - math.sqrt(1.27)) < 0.04, (c0, c1)
+    assert abs(c0 - 10.0 / 300.0) < 0.1 * 10.0 / 300.0, c0   # C lambda / N at u = 0

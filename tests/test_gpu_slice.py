@@ -130,3 +130,18 @@ def test_slice_every_launch_variant_bit_exact(variant):
     assert err == 0
     got = run_slice(L, 5, n0, 2, 4, flags=mclg.NO_STREAM, kernel_variant=variant)
     assert np.array_equal(got, want)
+
+
+def test_slice_galilean_rate_bit_exact():
+    """Slice tables built with each slice's Galilean-invariant rate, heavy nodes
+    with the sequential draws at their own rate."""
+    L = [64, 37, 300, 9]
+    g = np.random.default_rng(13)
+    S = sum(L)
+    n0 = np.stack([g.poisson(3, S), g.poisson(12, S), g.poisson(9, S)]).astype(np.uint16)
+    for n_max in (256, 20):
+        want, err = oracle.slice_step(L, 21, n0, 3, 12, lam=(3, 4), flags=oracle.FLAG_GALILEAN,
+                                      n_max=n_max)
+        assert err == 0
+        got = run_slice(L, 21, n0, 3, 12, lam=(3, 4), flags=mclg.GALILEAN, slice_n_max=n_max)
+        assert np.array_equal(got, want), n_max
