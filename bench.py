@@ -220,7 +220,7 @@ def run_reference(args):
     ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
     rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
     per_step = 120.0 / max(1, args.steps + args.warmup)
-    sw = sample_workload(wl, max(1024, int(rate * per_step)))
+    sw = sample_workload(wl, max(8, int(rate * per_step)))  # one 8-node chunk at least
     n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
     assert err == 0
     t = 0

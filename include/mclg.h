@@ -115,8 +115,8 @@ typedef struct {
                                4096; 0 = 256); a node with a larger mass takes the
                                SEQUENTIAL sampler's C decisions (the same bits that sampler
                                gives it).  The bits depend on slice_n_max like on the seed.
-                               Tables take about 672 (n+1)^3 / 12 bytes of device memory
-                               (1.0 GB at 256, 7.6 GB at 512); built once, at the first
+                               Tables take about 1184 (n+1)^3 / 12 bytes of device memory
+                               (1.7 GB at 256, 13.4 GB at 512); built once, at the first
                                mclg_step, on the host cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
                                 mclg_step; v + 1 = use variant v (0 <= v < 6; nodes per thread
@@ -217,10 +217,10 @@ mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int3
 /* The slice sampler's table row for the state (N, J, b) (host computation, no
  * GPU): F[k] = min(floor(CDF[dmin + k] 2^64), 2^64 - 1) for k < dmax - dmin,
  * the exact cumulative C-step law of the rest count (F holds 2C entries);
- * *dmin, *dmax the reachable offsets.  guide (256 uint16, or NULL) receives
+ * *dmin, *dmax the reachable offsets.  guide (512 uint16, or NULL) receives
  * the row's guide entries as the device reads them; for bucket j =
- * [j 2^56, (j+1) 2^56): bits 0-4 #{k : F[k] < j 2^56}, bits 5-6
- * min(#{k : F[k] in bucket j}, 3), bits 8-15 bits 55..48 of that F[k] when
+ * [j 2^55, (j+1) 2^55): bits 0-4 #{k : F[k] < j 2^55}, bits 5-6
+ * min(#{k : F[k] in bucket j}, 3), bits 8-15 bits 54..47 of that F[k] when
  * it is the only one in the bucket (else 0).
  * For checking the tables against an independent computation.  MCLG_ERR_ARG
  * for C > 10 or an invalid state. */

@@ -15,7 +15,7 @@ constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one per
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
 constexpr uint32_t kPersistentVariants = 3;      // register bounds of the persistent kernel
 constexpr int kSliceMaxC = 10;                   // slice sampler: sub-collisions per step
-constexpr int kSliceBucketBits = 8;              // guide table: buckets of the top bits of Q
+constexpr int kSliceBucketBits = 9;              // guide table: buckets of the top bits of Q
 constexpr int kSliceBuckets = 1 << kSliceBucketBits;
 constexpr int kSliceRowU64 = 20;                 // secondary row: 2C entries
 constexpr uint32_t kSliceMaxN = 4096;            // largest mass the slice tables may cover

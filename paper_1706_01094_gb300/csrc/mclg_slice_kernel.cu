@@ -12,12 +12,12 @@
 // or 16-byte vector per plane; replicas start on multiples of 8 nodes, so a
 // vector never straddles two).  Node pair (2i, 2i + 1) shares one Philox
 // block: node 2i takes words (0, 1), node 2i + 1 words (2, 3) as Q.  The
-// row's guide entry for the top 8 bits of Q gives the count directly unless
-// an F[k] falls inside Q's bucket (about 3% of nodes near equilibrium); then
+// row's guide entry for the top 9 bits of Q gives the count directly unless
+// an F[k] falls inside Q's bucket (about 1.6% of nodes near equilibrium); then
 // the entry also holds that F[k]'s next 8 bits, which decide Q against it
-// unless Q has the same 16 top bits (or several entries share the bucket,
+// unless Q has the same 17 top bits (or several entries share the bucket,
 // mostly in the tails): then Q is compared with the row's u64 entries from
-// the guide's count on (below 1% of nodes near equilibrium).
+// the guide's count on (about 0.5% of nodes near equilibrium).
 //
 // A node heavier than the tables' n_max takes the sequential sampler's C
 // decisions (the bits that sampler gives it) in a second, small pass of the
@@ -50,7 +50,7 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
         __ldg(tab.guide + (uint64_t(row) << kSliceBucketBits) + (hi >> (32 - kSliceBucketBits)));
     uint32_t count = e & 0x1Fu;
     const uint32_t inside = (e >> 5) & 3u;  // entries in Q's bucket (3: three or more)
-    const uint32_t qn = (hi >> (24 - kSliceBucketBits)) & 0xFFu, fn = e >> 8;  // Q bits 55..48
+    const uint32_t qn = (hi >> (24 - kSliceBucketBits)) & 0xFFu, fn = e >> 8;  // Q bits 54..47
     if (inside == 1u && qn != fn) {
         count += qn > fn ? 1u : 0u;  // the next 8 bits decide Q against that entry
     } else if (inside != 0u) {

@@ -4,7 +4,7 @@
 // one-sub-collision matrix), as exact fixed-point values
 //     F[d] = min(floor(CDF[d] 2^64), 2^64 - 1),   d = dmin .. dmax - 1,
 // stored per row re-based at dmin (the u64 secondary table), and a guide
-// table that the kernel reads first: for each of the 2^8 buckets of the top
+// table that the kernel reads first: for each of the 2^9 buckets of the top
 // bits of a 64-bit uniform Q, the number of entries below the bucket's start,
 // how many lie inside it and, when exactly one does, its next 8 bits, which
 // decide Q against it unless Q shares them too; the rest is decided on the
@@ -219,9 +219,9 @@ uint64_t slice_rows(uint32_t n_max)
     return rows;
 }
 
-// Guide row of one law, for each bucket j = [j 2^56, (j + 1) 2^56):
-// below = #{k : F[k] < j 2^56}, inside = #{k : F[k] in bucket j};
-// entry = below | min(inside, 3) << 5 | (inside == 1 ? bits 55..48 of that F : 0) << 8.
+// Guide row of one law, for each bucket j = [j 2^55, (j + 1) 2^55):
+// below = #{k : F[k] < j 2^55}, inside = #{k : F[k] in bucket j};
+// entry = below | min(inside, 3) << 5 | (inside == 1 ? bits 54..47 of that F : 0) << 8.
 void build_slice_guide(const uint64_t *F, int n, uint16_t *guide)
 {
     constexpr int kShift = 64 - kSliceBucketBits;

@@ -46,13 +46,13 @@ def test_rows_are_cumulative_and_symmetric(lib):
 
 
 def test_guide_rows_count_entries_below_each_bucket(lib):
-    """Guide entry j of a row (bucket [j 2^56, (j+1) 2^56)) holds #{k : F[k] below
+    """Guide entry j of a row (bucket [j 2^55, (j+1) 2^55)) holds #{k : F[k] below
     the bucket} (the oracle's F), min(#inside, 3) and, for a single entry inside,
-    its bits 55..48; a bucket with no entry decides #{k : Q > F[k]}, hence the new
+    its bits 54..47; a bucket with no entry decides #{k : Q > F[k]}, hence the new
     rest count, for all Q in it, and one with a single entry decides every Q whose
-    bits 55..48 differ from the entry's."""
+    bits 54..47 differ from the entry's."""
     rnd = random.Random(11)
-    for _ in range(150):
+    for _ in range(120):
         N = rnd.randint(2, 300)
         J = rnd.randint(-N, N)
         b = rnd.randrange((N - abs(J)) & 1, N - abs(J) + 1, 2)
@@ -61,16 +61,17 @@ def test_guide_rows_count_entries_below_each_bucket(lib):
         F, dmin, dmax, G = lib.slice_row(N, J, b, C, lam, guide=True)
         Fo, omin, omax = oracle.slice_cdf(N, J, b, C, lam)
         Fo = [int(Fo[d + C]) for d in range(omin, omax)]
-        for j in range(256):
-            below = sum(1 for f in Fo if f < j << 56)
-            ins = [f for f in Fo if j << 56 <= f < (j + 1) << 56]
-            next8 = (ins[0] >> 48) & 0xFF if len(ins) == 1 else 0
+        assert G.size == 512
+        for j in range(512):
+            below = sum(1 for f in Fo if f < j << 55)
+            ins = [f for f in Fo if j << 55 <= f < (j + 1) << 55]
+            next8 = (ins[0] >> 47) & 0xFF if len(ins) == 1 else 0
             assert int(G[j]) == below | min(len(ins), 3) << 5 | next8 << 8, (N, J, b, C, lam, j)
             if not ins:  # the count is the same for the bucket's first and last Q
-                for Q in (j << 56, ((j + 1) << 56) - 1):
+                for Q in (j << 55, ((j + 1) << 55) - 1):
                     assert oracle.slice_draw(N, J, b, Q, C, lam) == b + 2 * (omin + below)
-            elif len(ins) == 1 and 0 < next8 < 255:  # Q's bits 55..48 decide against it
-                lo_q = (j << 56) | ((next8 - 1) << 48) | ((1 << 48) - 1)
-                hi_q = (j << 56) | ((next8 + 1) << 48)
+            elif len(ins) == 1 and 0 < next8 < 255:  # Q's bits 54..47 decide against it
+                lo_q = (j << 55) | ((next8 - 1) << 47) | ((1 << 47) - 1)
+                hi_q = (j << 55) | ((next8 + 1) << 47)
                 assert oracle.slice_draw(N, J, b, lo_q, C, lam) == b + 2 * (omin + below)
                 assert oracle.slice_draw(N, J, b, hi_q, C, lam) == b + 2 * (omin + below + 1)
