@@ -59,6 +59,8 @@ def parse():
                          "(the persistent batched kernel); auto: slice for the single-lattice "
                          "and statistics workloads, sequential for the batches")
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
+    ap.add_argument("--slice-n-max", type=int, default=0,
+                    help="slice sampler: largest node mass the tables cover (0: the library's 256)")
     ap.add_argument("--kernel-variant", type=int, default=None,
                     help="fix the per-step kernel's launch variant (default: autotuned)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -316,7 +318,8 @@ def run_gb300(args):
     sampler = mclg.SAMPLER_SLICE if sampler_name == "slice" else mclg.SAMPLER_SEQUENTIAL
     lat = mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
                        first_replica=first, flags=mclg.STATS if stats_on else 0,
-                       sampler=sampler, kernel_variant=args.kernel_variant)
+                       sampler=sampler, kernel_variant=args.kernel_variant,
+                       slice_n_max=args.slice_n_max)
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 
