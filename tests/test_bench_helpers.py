@@ -1,0 +1,61 @@
+"""CPU checks of bench.py's bookkeeping: the launch count it reports, the sampler
+each workload uses by default, the figures it reads from the committed ncu
+summaries and the bounded samples the CPU oracle is timed on."""
+import types
+
+import numpy as np
+import pytest
+
+import bench
+from paper_1706_01094_gb300 import workloads
+
+MODES = types.SimpleNamespace(MODE_AUTO=0, MODE_PLAIN=1, MODE_PERSISTENT=2, MODE_BATCHED=3)
+
+
+def test_launch_counts_follow_the_library_schedule():
+    single = workloads.single()
+    batched = workloads.batched()
+    # slice sampler: table kernel + heavy-node pass per step, one time-advance
+    # kernel per 32-step graph and one time-set kernel per call
+    assert bench.count_launches(10000, single, 0, False, False, MODES, True) == 20000 + 312 + 1
+    assert bench.count_launches(31, single, 0, False, False, MODES, True) == 62   # no graph
+    assert bench.count_launches(64, single, 0, False, True, MODES, True) == 64 * 5 + 2 + 1
+    # per-replica launches of the baseline mode
+    assert bench.count_launches(3, batched, MODES.MODE_PLAIN, False, False, MODES, True) \
+        == 3 * batched.replicas * 2
+    assert bench.count_launches(3, batched, MODES.MODE_PLAIN, False, False, MODES) \
+        == 3 * batched.replicas
+    # sequential persistent: one launch per call of at most 65536 steps
+    assert bench.count_launches(2000, batched, 0, True, False, MODES) == 1
+
+
+def test_default_sampler_per_workload():
+    for name, want in (("single", "slice"), ("fluct", "slice"), ("batched", "sequential"),
+                       ("uneven", "sequential"), ("small", "sequential")):
+        args = types.SimpleNamespace(sampler="auto", workload=name)
+        assert bench.pick_sampler(args) == want
+    assert bench.pick_sampler(types.SimpleNamespace(sampler="sequential", workload="single")) \
+        == "sequential"
+
+
+def test_committed_profile_figures():
+    traffic = bench.committed_figure("k_step_slice", "single")
+    assert traffic is not None and 1e8 < traffic < 4e8   # bytes per launch of a 2^24-node step
+    for key in ("alu_pipe_pct", "issue_active_pct"):
+        v = bench.committed_figure("k_step_slice", "single", key)
+        assert v is not None and 0 < v <= 100
+    assert bench.committed_figure("k_step_slice", "no_such_workload") is None
+    assert bench.committed_figure("k_step_persistent", "batched") is not None
+
+
+@pytest.mark.parametrize("name", ["single", "batched", "uneven"])
+def test_oracle_samples_are_bounded_slices_of_the_workload(name):
+    wl = workloads.BY_NAME[name]()
+    sw = bench.sample_workload(wl, 5000)
+    assert 8 <= sw.nodes <= max(5000, int(wl.L.max())) and sw.nodes == int(sw.L.sum())
+    assert sw.rho.size == sw.nodes and sw.u.size == sw.nodes
+    if wl.replicas > 1:   # whole replicas from the front, same profiles
+        k = sw.replicas
+        assert np.array_equal(sw.L, wl.L[:k]) and np.array_equal(sw.rho, wl.rho[:sw.nodes])
+    tiny = bench.sample_workload(wl, 1)
+    assert tiny.nodes >= 8 or wl.replicas > 1
