@@ -281,17 +281,17 @@ def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=Fa
     """Our kernels launched by one mclg_step(steps) call, as the library issues them."""
     if slice_sampler:
         # per step: the table kernel and the sequential pass over heavy nodes
-        # (+ statistics: 2 passes and the count)
+        # (+ statistics: 2 passes)
         if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
             return steps * wl.replicas * 2
-        return graph_launches(steps, 5 if stats_on else 2)
+        return graph_launches(steps, 4 if stats_on else 2)
     if persistent:
         long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
         # one persistent launch per 65536 steps, plus the long replicas' batched plain steps
         return -(-steps // 65536) + (graph_launches(steps, 1) if long_replicas else 0)
     if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
         return steps * wl.replicas  # the per-replica baseline, launched directly
-    return graph_launches(steps, 4 if stats_on else 1)  # step (+ statistics: 2 passes, count)
+    return graph_launches(steps, 3 if stats_on else 1)  # step (+ statistics: 2 passes)
 
 
 def run_gb300(args):

@@ -768,7 +768,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
             !alloc((void **)&h->st.mean32c, Lc * 3 * sizeof(float)) ||
             !alloc((void **)&h->st.m2, Lc * 6 * sizeof(float)) ||
             !alloc((void **)&h->st.m2c, Lc * 6 * sizeof(float)) ||
-            !alloc((void **)&h->st.count, sizeof(unsigned long long)) ||
+            !alloc((void **)&h->st.count, 2 * sizeof(unsigned long long)) ||
             !alloc((void **)&h->d_stat_partials, stats_partials_bytes(Lc, replicas)))
             return fail(MCLG_ERR_NOMEM);
         *out = h;
@@ -971,7 +971,7 @@ mclg_status mclg_stats_reset(mclg_handle h)
     MCLG_CK(cudaMemsetAsync(h->st.mean32c, 0, Lc * 3 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.m2, 0, Lc * 6 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.m2c, 0, Lc * 6 * sizeof(float), h->stream));
-    MCLG_CK(cudaMemsetAsync(h->st.count, 0, sizeof(unsigned long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.count, 0, 2 * sizeof(unsigned long long), h->stream));
     MCLG_CK(cudaMemsetAsync(h->d_stat_partials, 0, stats_partials_bytes(uint32_t(Lc), h->R),
                             h->stream));
     h->stats_count = 0;

@@ -84,7 +84,7 @@ struct StatsBuffers {
     long long *s1, *s2, *snb;   // [L*3], [L*6], [L*9]
     float *mean32, *mean32c;    // [L*3] running means and their compensation
     float *m2, *m2c;            // [L*6] running co-moments and their compensation
-    unsigned long long *count;  // samples per position
+    unsigned long long *count;  // [2]: samples per position, finishing ticket of the merge pass
 };
 
 cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);

@@ -358,33 +358,59 @@ __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restric
     const uint32_t slice = blockIdx.y;
     const uint32_t r_begin = uint32_t(uint64_t(R) * slice / slices);
     const uint32_t r_end = uint32_t(uint64_t(R) * (slice + 1) / slices);
-    unsigned long long acc[kStatQ];
+    __shared__ unsigned long long red[8][32][kStatQ + 1];  // <= 8 groups; +1 avoids bank conflicts
+    unsigned long long *mine = red[grp][xl];
 #pragma unroll
-    for (int q = 0; q < kStatQ; ++q) acc[q] = 0;
+    for (int q = 0; q < kStatQ; ++q) mine[q] = 0ull;
     if (x < L) {
         const uint32_t x1 = x + 1u == L ? 0u : x + 1u;  // neighbour position
         const uint32_t xr = stream ? (x + 1u == L ? 0u : x + 1u) : x;
         const uint32_t xlft = stream ? (x == 0u ? L - 1u : x - 1u) : x;
         const uint32_t x1r = stream ? (x1 + 1u == L ? 0u : x1 + 1u) : x1;
         const uint32_t x1l = stream ? (x1 == 0u ? L - 1u : x1 - 1u) : x1;
+        // At most 16 replicas per thread (the launch sizes the slices so): with
+        // every value below 2^14 each product is below 2^28 and 16 of them fit
+        // 32 bits, so the sums run in 32-bit multiply-adds; a thread that saw a
+        // larger value redoes its replicas with 64-bit sums (in shared memory).
+        uint32_t a32[kStatQ];
+#pragma unroll
+        for (int q = 0; q < kStatQ; ++q) a32[q] = 0u;
+        uint32_t big = 0;
+#pragma unroll 4
         for (uint32_t r = r_begin + grp; r < r_end; r += ngrp) {
-            const uint64_t base = r * stride;
-            const uint32_t v0 = B[base + xr], v1 = B[P + base + x], v2 = B[2 * P + base + xlft];
-            const uint32_t w0 = B[base + x1r], w1 = B[P + base + x1], w2 = B[2 * P + base + x1l];
-            // every product of two uint16 values fits 32 bits
-            acc[0] += v0; acc[1] += v1; acc[2] += v2;
-            acc[3] += v0 * v0; acc[4] += v0 * v1; acc[5] += v0 * v2;
-            acc[6] += v1 * v1; acc[7] += v1 * v2; acc[8] += v2 * v2;
-            acc[9] += v0 * w0; acc[10] += v0 * w1; acc[11] += v0 * w2;
-            acc[12] += v1 * w0; acc[13] += v1 * w1; acc[14] += v1 * w2;
-            acc[15] += v2 * w0; acc[16] += v2 * w1; acc[17] += v2 * w2;
+            const uint16_t *row = B + r * stride;
+            const uint32_t v0 = row[xr], v1 = row[P + x], v2 = row[2 * P + xlft];
+            const uint32_t w0 = row[x1r], w1 = row[P + x1], w2 = row[2 * P + x1l];
+            big |= v0 | v1 | v2 | w0 | w1 | w2;
+            a32[0] += v0; a32[1] += v1; a32[2] += v2;
+            a32[3] += v0 * v0; a32[4] += v0 * v1; a32[5] += v0 * v2;
+            a32[6] += v1 * v1; a32[7] += v1 * v2; a32[8] += v2 * v2;
+            a32[9] += v0 * w0; a32[10] += v0 * w1; a32[11] += v0 * w2;
+            a32[12] += v1 * w0; a32[13] += v1 * w1; a32[14] += v1 * w2;
+            a32[15] += v2 * w0; a32[16] += v2 * w1; a32[17] += v2 * w2;
+        }
+        if (big < (1u << 14)) {
+#pragma unroll
+            for (int q = 0; q < kStatQ; ++q) mine[q] = a32[q];
+        } else {
+            for (uint32_t r = r_begin + grp; r < r_end; r += ngrp) {
+                const uint16_t *row = B + r * stride;
+                const uint64_t v[3] = {row[xr], row[P + x], row[2 * P + xlft]};
+                const uint64_t w[3] = {row[x1r], row[P + x1], row[2 * P + x1l]};
+                for (int i = 0; i < 3; ++i) mine[i] += v[i];
+                int q = 3;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = i; j < 3; ++j) mine[q++] += v[i] * v[j];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) mine[q++] += v[i] * w[j];
+            }
         }
     }
-    __shared__ unsigned long long red[8][32][kStatQ + 1];  // <= 8 groups; +1 avoids bank conflicts
-#pragma unroll
-    for (int q = 0; q < kStatQ; ++q) red[grp][xl][q] = acc[q];
     __syncthreads();
     if (grp != 0 || x >= L) return;
+    unsigned long long acc[kStatQ];
+#pragma unroll
+    for (int q = 0; q < kStatQ; ++q) acc[q] = mine[q];
     for (uint32_t g2 = 1; g2 < ngrp; ++g2)
 #pragma unroll
         for (int q = 0; q < kStatQ; ++q) acc[q] += red[g2][xl][q];
@@ -396,7 +422,8 @@ __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restric
 // Pass 2: thread (position, quantity) adds its batch sum to the int64
 // accumulator and clears it; then one thread per position merges the batch
 // into the FP32 running means and co-moments (Chan et al.), with Kahan
-// compensation, reading the batch from shared memory.
+// compensation, reading the batch from shared memory.  count[0] holds the
+// samples per position so far; count[1] is the blocks' finishing ticket.
 constexpr uint32_t kMergePositions = 14;  // 14 x 18 = 252 threads per block
 
 __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restrict__ batch,
@@ -415,38 +442,47 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
         else st.snb[9u * x + (q - 9)] += v;
     }
     __syncthreads();
-    if (threadIdx.x >= kMergePositions) return;
     const uint32_t xm = blockIdx.x * kMergePositions + threadIdx.x;
-    if (xm >= L) return;
-    const long long *acc = sb[threadIdx.x];
-    const float Rb = float(R);
-    const float Ma = float(*st.count);  // samples per position before this batch
-    const float Mt = Ma + Rb;
-    float delta[3];
-    for (int i = 0; i < 3; ++i) {
-        const float mb = float(acc[i]) / Rb;
-        const float m = st.mean32[3u * xm + i];
-        delta[i] = mb - m;
-        const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * xm + i];
-        const float nm = m + inc;
-        st.mean32c[3u * xm + i] = (nm - m) - inc;
-        st.mean32[3u * xm + i] = nm;
+    if (threadIdx.x < kMergePositions && xm < L) {
+        const long long *acc = sb[threadIdx.x];
+        const float Rb = float(R);
+        const float Ma = float(*st.count);  // samples per position before this batch
+        const float Mt = Ma + Rb;
+        float delta[3];
+        for (int i = 0; i < 3; ++i) {
+            const float mb = float(acc[i]) / Rb;
+            const float m = st.mean32[3u * xm + i];
+            delta[i] = mb - m;
+            const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * xm + i];
+            const float nm = m + inc;
+            st.mean32c[3u * xm + i] = (nm - m) - inc;
+            st.mean32[3u * xm + i] = nm;
+        }
+        const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k) {
+            const int i = pi[k], j = pj[k];
+            // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (R s_ij - s_i s_j) / R, exact numerator
+            const long long num = (long long)R * acc[3 + k] - acc[i] * acc[j];
+            const float cb = float(num) / Rb;
+            const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * xm + k];
+            const float m2 = st.m2[6u * xm + k];
+            const float nm2 = m2 + inc;
+            st.m2c[6u * xm + k] = (nm2 - m2) - inc;
+            st.m2[6u * xm + k] = nm2;
+        }
     }
-    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
-    for (int k = 0; k < 6; ++k) {
-        const int i = pi[k], j = pj[k];
-        // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (R s_ij - s_i s_j) / R, exact numerator
-        const long long num = (long long)R * acc[3 + k] - acc[i] * acc[j];
-        const float cb = float(num) / Rb;
-        const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * xm + k];
-        const float m2 = st.m2[6u * xm + k];
-        const float nm2 = m2 + inc;
-        st.m2c[6u * xm + k] = (nm2 - m2) - inc;
-        st.m2[6u * xm + k] = nm2;
+    // the last block to finish, after every block has read the count, adds
+    // this step's R samples to it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(st.count + 1, 1ull) == gridDim.x - 1u) {
+            st.count[0] += R;
+            st.count[1] = 0ull;
+            __threadfence();
+        }
     }
 }
-
-__global__ void k_count_add(unsigned long long *count, uint32_t R) { *count += R; }
 
 __global__ void k_set_time(uint32_t *t_dev, uint32_t value) { *t_dev = value; }
 __global__ void k_advance_time(uint32_t *t_dev, uint32_t by) { *t_dev += by; }
@@ -571,7 +607,9 @@ cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layo
     return cudaGetLastError();
 }
 
-uint32_t stats_slices(uint32_t R) { return std::min<uint32_t>(16u, std::max<uint32_t>(1u, R / 8u)); }
+// Replica slices of the partial-sum pass: each of its 8 thread groups takes at
+// most 16 replicas of a slice (the bound its 32-bit sums rely on).
+uint32_t stats_slices(uint32_t R) { return std::max<uint32_t>(1u, (R + 127u) / 128u); }
 
 size_t stats_partials_bytes(uint32_t L, uint32_t R)
 {
@@ -589,8 +627,6 @@ cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, R, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_count_add<<<1, 1, 0, s>>>(st.count, R);
     return cudaGetLastError();
 }
 
