@@ -277,21 +277,30 @@ def graph_launches(steps: int, per_step: int) -> int:
     return steps * per_step + groups + (1 if groups else 0)
 
 
+def stats_merges(steps: int) -> int:
+    """Merge passes of the statistics: one per 32-step graph, one for the rest."""
+    return steps // GRAPH_STEPS + (1 if steps % GRAPH_STEPS else 0)
+
+
 def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=False):
     """Our kernels launched by one mclg_step(steps) call, as the library issues them."""
     if slice_sampler:
         # per step: the table kernel and the sequential pass over heavy nodes
-        # (+ statistics: 2 passes)
+        # (+ statistics: the partial pass every step, the merge pass per batch)
         if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
             return steps * wl.replicas * 2
-        return graph_launches(steps, 4 if stats_on else 2)
+        if stats_on:
+            return graph_launches(steps, 3) + stats_merges(steps)
+        return graph_launches(steps, 2)
     if persistent:
         long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
         # one persistent launch per 65536 steps, plus the long replicas' batched plain steps
         return -(-steps // 65536) + (graph_launches(steps, 1) if long_replicas else 0)
     if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
         return steps * wl.replicas  # the per-replica baseline, launched directly
-    return graph_launches(steps, 3 if stats_on else 1)  # step (+ statistics: 2 passes)
+    if stats_on:  # step, partial pass per step, merge pass per batch
+        return graph_launches(steps, 2) + stats_merges(steps)
+    return graph_launches(steps, 1)
 
 
 def run_gb300(args):
@@ -371,7 +380,7 @@ def run_gb300(args):
         var64 = st["cov64"][:, [0, 3, 5]]
         scale = np.sqrt(var64[:, [0, 0, 1]] * var64[:, [1, 2, 2]])
         cnt = st["count"]
-        mean = st["s1"].sum(axis=0) / (cnt * wl.L[0])
+        mean = st["s1"].sum(axis=0) / (float(cnt) * float(wl.L[0]))  # no uint32 product
         stats_summary = {
             "samples_per_position": cnt,
             "fp32_var_max_rel_err_vs_fp64": float((np.abs(var32 - var64) / var64).max()),

@@ -349,9 +349,16 @@ cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t
     cudaError_t e = plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], t, kb, ke, s, t_dev);
     if (e != cudaSuccess) return e;
     if (h->prm.flags & MCLG_STATS)
-        e = launch_stats(h->d_B[c ^ 1], h->lay.P, h->L[0], h->R, pad8(h->L[0]), streaming(h) ? 1 : 0,
-                         h->st, h->d_stat_partials, s);
+        e = launch_stats_partial(h->d_B[c ^ 1], h->lay.P, h->L[0], h->R, pad8(h->L[0]),
+                                 streaming(h) ? 1 : 0, h->d_stat_partials, s);
     return e;
+}
+
+// Fold the statistics of the last `steps` steps into the running moments.
+cudaError_t stats_merge(mclg_ctx *h, uint64_t steps, cudaStream_t s)
+{
+    if (!(h->prm.flags & MCLG_STATS) || steps == 0) return cudaSuccess;
+    return launch_stats_merge(h->d_stat_partials, h->L[0], steps * h->R, h->st, s);
 }
 
 void drop_graphs(mclg_ctx *h)
@@ -380,6 +387,7 @@ mclg_status capture_graph(mclg_ctx *h, int c, uint32_t kb, uint32_t ke)
         e = plain_step_seq(h, cc, j, kb, ke, h->cap, h->d_t);
         cc ^= 1;
     }
+    if (e == cudaSuccess) e = stats_merge(h, kGraphSteps, h->cap);  // one merge per graph
     if (e == cudaSuccess) e = launch_advance_time(h->d_t, kGraphSteps, h->cap);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -407,10 +415,12 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
         for (uint64_t g = 0; g < groups; ++g) MCLG_CK(cudaGraphLaunch(h->graph[c], s));
         done = groups * kGraphSteps;  // even: the parity of c is unchanged
     }
+    const uint64_t rest = n_steps - done;
     for (; done < n_steps; ++done) {
         MCLG_CK(plain_step_seq(h, c, t + done, kb, ke, s, nullptr));
         c ^= 1;
     }
+    MCLG_CK(stats_merge(h, rest, s));  // every call leaves the statistics merged
     *c_out = c;
     return MCLG_OK;
 }

@@ -125,9 +125,14 @@ cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, 
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
                            unsigned long long *totals, cudaStream_t s);
 size_t stats_partials_bytes(uint32_t L, uint32_t R);
-cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
-                         int stream, const StatsBuffers &st, unsigned long long *partials,
-                         cudaStream_t s);
+// Statistics: the partial pass adds one step's exact sums to the batch sums;
+// the merge pass folds a batch of n samples per position (steps x R) into the
+// int64 accumulators and the FP32 running moments and clears the batch.
+cudaError_t launch_stats_partial(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R,
+                                 uint64_t stride, int stream, unsigned long long *batch,
+                                 cudaStream_t s);
+cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, uint64_t n,
+                               const StatsBuffers &st, cudaStream_t s);
 cudaError_t launch_set_time(uint32_t *t_dev, uint32_t value, cudaStream_t s);
 cudaError_t launch_advance_time(uint32_t *t_dev, uint32_t by, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint32_t *out,

@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restric
 constexpr uint32_t kMergePositions = 14;  // 14 x 18 = 252 threads per block
 
 __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restrict__ batch,
-                                                     uint32_t L, uint32_t R, StatsBuffers st)
+                                                     uint32_t L, uint64_t n, StatsBuffers st)
 {
     __shared__ long long sb[kMergePositions][kStatQ];
     const uint32_t lp = threadIdx.x / kStatQ, q = threadIdx.x % kStatQ;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
     const uint32_t xm = blockIdx.x * kMergePositions + threadIdx.x;
     if (threadIdx.x < kMergePositions && xm < L) {
         const long long *acc = sb[threadIdx.x];
-        const float Rb = float(R);
+        const float Rb = float(n);  // samples per position in this batch
         const float Ma = float(*st.count);  // samples per position before this batch
         const float Mt = Ma + Rb;
         float delta[3];
@@ -461,8 +461,8 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
         const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
         for (int k = 0; k < 6; ++k) {
             const int i = pi[k], j = pj[k];
-            // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (R s_ij - s_i s_j) / R, exact numerator
-            const long long num = (long long)R * acc[3 + k] - acc[i] * acc[j];
+            // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (n s_ij - s_i s_j) / n, exact numerator
+            const __int128 num = (__int128)n * acc[3 + k] - (__int128)acc[i] * acc[j];
             const float cb = float(num) / Rb;
             const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * xm + k];
             const float m2 = st.m2[6u * xm + k];
@@ -472,12 +472,12 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
         }
     }
     // the last block to finish, after every block has read the count, adds
-    // this step's R samples to it
+    // this batch's n samples to it
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(st.count + 1, 1ull) == gridDim.x - 1u) {
-            st.count[0] += R;
+            st.count[0] += n;
             st.count[1] = 0ull;
             __threadfence();
         }
@@ -617,16 +617,20 @@ size_t stats_partials_bytes(uint32_t L, uint32_t R)
     return size_t(L) * kStatQ * sizeof(unsigned long long);
 }
 
-cudaError_t launch_stats(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R, uint64_t stride,
-                         int stream, const StatsBuffers &st, unsigned long long *batch,
-                         cudaStream_t s)
+cudaError_t launch_stats_partial(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R,
+                                 uint64_t stride, int stream, unsigned long long *batch,
+                                 cudaStream_t s)
 {
     const uint32_t slices = stats_slices(R);
     const dim3 grid((L + 31) / 32, slices);
     k_stats_partial<<<grid, 256, 0, s>>>(B, P, L, R, stride, stream, slices, batch);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, R, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, uint64_t n,
+                               const StatsBuffers &st, cudaStream_t s)
+{
+    k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, n, st);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,8 @@ def test_launch_counts_follow_the_library_schedule():
     # kernel per 32-step graph and one time-set kernel per call
     assert bench.count_launches(10000, single, 0, False, False, MODES, True) == 20000 + 312 + 1
     assert bench.count_launches(31, single, 0, False, False, MODES, True) == 62   # no graph
-    assert bench.count_launches(64, single, 0, False, True, MODES, True) == 64 * 4 + 2 + 1
+    assert bench.count_launches(64, single, 0, False, True, MODES, True) == 64 * 3 + 2 + 1 + 2
+    assert bench.count_launches(70, single, 0, False, True, MODES, True) == 70 * 3 + 2 + 1 + 3
     # per-replica launches of the baseline mode
     assert bench.count_launches(3, batched, MODES.MODE_PLAIN, False, False, MODES, True) \
         == 3 * batched.replicas * 2

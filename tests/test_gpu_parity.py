@@ -418,3 +418,33 @@ def test_galilean_rate_bit_exact(mode):
     assert err == 0
     got = run_gpu(L, 21, n0, 3, 12, lam=(3, 4), flags=mclg.GALILEAN, mode=mode)
     assert np.array_equal(got, want)
+
+
+def test_statistics_merged_at_the_end_of_every_call():
+    """The FP32 running moments take the exact sums in batches (one per 32-step
+    graph and one per call); after calls of 7, 40 and 1 steps, each read gives the
+    oracle's exact sums and FP32 (co)variances within 1e-6 of the exact ones."""
+    R, Lc = 40, 96
+    L = np.full(R, Lc, dtype=np.uint32)
+    wl = workloads.fluct(R=R, L=Lc, rho=30.0, u=0.1)
+    n0, err = oracle.init(L, 3, wl.rho, wl.u)
+    assert err == 0
+    ref = oracle.Stats(Lc, R)
+    n, t = n0, 0
+    with mclg.Lattice(L, seed=3, flags=mclg.STATS, sampler=mclg.SAMPLER_SLICE) as lat:
+        lat.set_state(n0, t=0)
+        lat.stats_reset()
+        for steps in (7, 40, 1):
+            lat.step(steps)
+            for _ in range(steps):
+                n, err = oracle.slice_step(L, 3, n, t, 1)
+                assert err == 0
+                ref.accumulate(n)
+                t += 1
+            st = lat.stats_read()
+            assert st["count"] == ref.count == t * R
+            assert np.array_equal(st["s1"], ref.s1) and np.array_equal(st["s2"], ref.s2)
+            assert np.array_equal(st["snb"], ref.snb)
+            var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
+            var64 = st["cov64"][:, [0, 3, 5]]
+            assert (np.abs(var32 - var64) / np.abs(var64)).max() <= 1e-6
