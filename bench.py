@@ -33,13 +33,23 @@ if ROOT not in sys.path:
 
 from paper_1706_01094_gb300 import workloads  # noqa: E402
 
-METRIC = "MCLG site updates/sec (GSUPS), D1Q3 C=10 lambda=1, bit-exact vs CPU oracle"
+
+
+def metric(C: int = 10) -> str:
+    return f"MCLG site updates/sec (GSUPS), D1Q3 C={C} lambda=1, bit-exact vs CPU oracle"
+
+
 BYTES_PER_NODE_STEP = 12        # 3 uint16 read + 3 uint16 written
-# Algorithmic integer operations per node-step at C <= 10 (one Philox block):
-# Philox4x32-10 = 10 rounds x (2 mul-hi + 2 mul-lo + 4 xor) + 9 x 2 key adds = 98;
-# each sub-collision = 3 mul (a c, b (b-1), q D) + 2 shifts + 1 add (thresholds)
-# + 4 compares + 3 adds (state update) = 13, times C = 10.
-INT_OPS_PER_NODE_STEP = 98 + 13 * 10
+
+
+def int_ops_per_node_step(C: int) -> int:
+    """Algorithmic integer operations of the sequential sampler per node-step: one
+    Philox4x32-10 block per 10 decisions = 10 rounds x (2 mul-hi + 2 mul-lo + 4 xor)
+    + 9 x 2 key adds = 98; each sub-collision = 3 mul (a c, b (b-1), q D) + 2 shifts
+    + 1 add (thresholds) + 4 compares + 3 adds (state update) = 13."""
+    return 98 * max(1, -(-C // 10)) + 13 * C
+
+
 INT32_LANES_PER_SM_CLK = 64     # integer pipe lanes per SM and clock
 SMS = 152
 
@@ -53,6 +63,8 @@ def parse():
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "uneven", "small", "fluct"])
     ap.add_argument("--u", type=float, default=0.2, help="velocity of the fluct workload")
+    ap.add_argument("--C", type=int, default=10,
+                    help="sub-collisions per node and step (the paper's runs: 10)")
     ap.add_argument("--sampler", default="auto", choices=["auto", "slice", "sequential"],
                     help="slice: the C sub-collisions of a node drawn at once from exact "
                          "cumulative-law tables; sequential: one sub-collision at a time "
@@ -160,9 +172,10 @@ def dist_env():
 
 
 def make_workload(name: str, args=None):
-    if name == "fluct":
-        return workloads.fluct(u=args.u if args is not None else 0.2)
-    return workloads.BY_NAME[name]()
+    from dataclasses import replace
+    wl = workloads.fluct(u=args.u if args is not None else 0.2) if name == "fluct" \
+        else workloads.BY_NAME[name]()
+    return replace(wl, C=args.C) if args is not None and getattr(args, "C", None) else wl
 
 
 def sample_workload(wl, nodes: int):
@@ -237,7 +250,7 @@ def run_reference(args):
     value = sw.nodes * args.steps / dt / 1e9
     sample = (f"each step: one time step of a {sw.nodes}-node, {sw.replicas}-replica sample of "
               f"the workload (same profile values)")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GSUPS",
+    line = {"impl": "reference", "metric": metric(wl.C), "value": value, "unit": "GSUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak" if wl.replicas == 1 else "strong",
@@ -437,18 +450,18 @@ def run_gb300(args):
                                                                  "issue_active_pct"),
                         "time_basis": "whole step (table kernel + heavy-node pass) per step"}
         else:
-            achieved_ops = INT_OPS_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
+            achieved_ops = int_ops_per_node_step(wl.C) * wl.nodes * args.steps / (ms / 1e3) / 1e9
             kernel = ("k_step_plain" if (wl.replicas == 1 or args.mode in ("plain", "batched"))
                       else "k_step_persistent")
             roofline = {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
                         "unit": "Gop/s", "frac": achieved_ops / alu_peak,
                         "traffic": committed_figure(kernel, wl.name), "kernel": kernel,
-                        "ops_per_node_step": INT_OPS_PER_NODE_STEP,
+                        "ops_per_node_step": int_ops_per_node_step(wl.C),
                         "peak_basis": (f"{INT32_LANES_PER_SM_CLK} int32 lanes x {SMS} SMs x "
                                        f"{sm_max:.0f} MHz"),
                         "hbm": hbm}
         line = {
-            "metric": METRIC, "value": value, "unit": "GSUPS", "n_gpus": world,
+            "metric": metric(wl.C), "value": value, "unit": "GSUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True,
             "scaling": "weak" if wl_full.replicas == 1 else "strong",

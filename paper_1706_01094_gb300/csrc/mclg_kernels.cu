@@ -608,8 +608,11 @@ cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layo
 }
 
 // Replica slices of the partial-sum pass: each of its 8 thread groups takes at
-// most 16 replicas of a slice (the bound its 32-bit sums rely on).
-uint32_t stats_slices(uint32_t R) { return std::max<uint32_t>(1u, (R + 127u) / 128u); }
+// most kStatReplicas replicas of a slice (<= 16, the bound its 32-bit sums rely
+// on; 4 measured slower on the statistics workload: the atomics outweigh the
+// extra CTAs).
+constexpr uint32_t kStatReplicas = 16;
+uint32_t stats_slices(uint32_t R) { return std::max<uint32_t>(1u, (R + 8u * kStatReplicas - 1u) / (8u * kStatReplicas)); }
 
 size_t stats_partials_bytes(uint32_t L, uint32_t R)
 {

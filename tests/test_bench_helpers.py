@@ -60,3 +60,13 @@ def test_oracle_samples_are_bounded_slices_of_the_workload(name):
         assert np.array_equal(sw.L, wl.L[:k]) and np.array_equal(sw.rho, wl.rho[:sw.nodes])
     tiny = bench.sample_workload(wl, 1)
     assert tiny.nodes >= 8 or wl.replicas > 1
+
+
+def test_op_tally_and_metric_follow_C():
+    assert bench.int_ops_per_node_step(10) == 228
+    assert bench.int_ops_per_node_step(1) == 98 + 13
+    assert bench.int_ops_per_node_step(23) == 3 * 98 + 13 * 23
+    assert "C=10" in bench.metric(10) and "C=1 " in bench.metric(1)
+    args = types.SimpleNamespace(u=0.2, C=1)
+    assert bench.make_workload("single", args).C == 1
+    assert bench.make_workload("fluct", types.SimpleNamespace(u=0.0, C=10)).C == 10
