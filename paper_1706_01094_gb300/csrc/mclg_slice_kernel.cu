@@ -106,16 +106,20 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
     const uint16_t *__restrict__ inm = p.in;
     const uint16_t *__restrict__ in0 = p.in + p.P;
     const uint16_t *__restrict__ inp = p.in + 2 * p.P;
+    // halo: lanes at a warp or replica edge load theirs directly, issued together
+    // with the vector loads; the others take them from the neighbouring lanes
+    const bool own_next = !(lane < 31u && x0 + V < L), own_prev = !(lane > 0u && x0 > 0u);
+    uint32_t nxt_own = 0u, prv_own = 0u;
+    if (kStream && own_next) nxt_own = inm[off + (x0 + V < L ? x0 + V : 0u)];
+    if (kStream && own_prev) prv_own = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
     uint32_t em[V], e0[V], ep[V];
     unpack(__ldcs(reinterpret_cast<const T *>(inm + node0)), em);
     unpack(__ldcs(reinterpret_cast<const T *>(in0 + node0)), e0);
     unpack(__ldcs(reinterpret_cast<const T *>(inp + node0)), ep);
     uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
     uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
-    if (kStream) {
-        if (!(lane < 31u && x0 + V < L)) nxt = inm[off + (x0 + V < L ? x0 + V : 0u)];
-        if (!(lane > 0u && x0 > 0u)) prv = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
-    }
+    if (kStream && own_next) nxt = nxt_own;
+    if (kStream && own_prev) prv = prv_own;
     // valid nodes here (none when the whole vector is replica padding)
     const uint32_t nv = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
     const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
