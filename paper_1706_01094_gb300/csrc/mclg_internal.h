@@ -10,6 +10,7 @@
 namespace mclg {
 
 constexpr uint32_t kPlainThreads = 256;          // threads per CTA of the plain kernel
+constexpr uint32_t kSliceThreads = 128;          // threads per CTA of the slice kernel (measured best)
 constexpr uint32_t kPersistentMaxThreads = 512;  // upper bound on persistent CTA size
 constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one persistent CTA
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA

@@ -75,8 +75,10 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
     return false;
 }
 
+// kMinBlocks counts CTAs of 256 threads (the register bound of the variant
+// table); the kernel runs CTAs of kSliceThreads.
 template <int V, int kMinBlocks, bool kOne>
-__global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
+__global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThreads)
     k_step_slice(PlainArgs p, SliceTables tab)
 {
     static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
@@ -238,9 +240,9 @@ template <int V, int kMinBlocks>
 static void launch_slice_v(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s)
 {
     const uint64_t threads = (p.g_end - p.g_begin) * (8u / V);
-    const dim3 grid(uint32_t((threads + kPlainThreads - 1) / kPlainThreads));
-    if (one) k_step_slice<V, kMinBlocks, true><<<grid, kPlainThreads, 0, s>>>(p, tab);
-    else k_step_slice<V, kMinBlocks, false><<<grid, kPlainThreads, 0, s>>>(p, tab);
+    const dim3 grid(uint32_t((threads + kSliceThreads - 1) / kSliceThreads));
+    if (one) k_step_slice<V, kMinBlocks, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    else k_step_slice<V, kMinBlocks, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
 }
 
 // Slice-kernel variants: (nodes per thread, minimum CTAs of 256 threads per
