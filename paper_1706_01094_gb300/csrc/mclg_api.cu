@@ -482,6 +482,7 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     h->slice.heavy_pos = h->d_heavy_pos;
     h->slice.heavy_ctl = h->d_heavy_ctl;
     h->slice.heavy_cap = kHeavyCap;
+    h->slice.guide_narrow = guide.size() <= size_t(0xFFFFFFFFu) ? 1u : 0u;
     drop_graphs(h);  // captured launches hold the old table pointers
     return MCLG_OK;
 }

@@ -107,6 +107,7 @@ struct SliceTables {
     unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
     uint32_t *heavy_ctl;            // {count, overflow, blocks done}, zero between steps
     uint32_t heavy_cap;
+    uint32_t guide_narrow;          // 1: every guide index fits 32 bits (rows < 2^32 / buckets)
 };
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
 constexpr uint32_t kHeavyBlocks = 304;           // CTAs of the heavy-node pass

@@ -36,6 +36,7 @@ namespace mclg {
 
 // One node's table draw.  Returns true, leaving the node as it is, when its
 // mass is beyond the tables (the sequential pass collides it).
+template <bool kNarrow>
 __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t lo,
                                            uint32_t hi, const SliceTables &tab, uint32_t C,
                                            uint32_t &err)
@@ -46,8 +47,11 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
     const uint32_t Jp = a > c ? a - c : c - a;
     const uint32_t below = (b - ((N - Jp) & 1u)) >> 1;
     const uint32_t row = __ldg(tab.rowstart + N * (tab.n_max + 1u) + Jp) + below;
-    const uint32_t e =
-        __ldg(tab.guide + (uint64_t(row) << kSliceBucketBits) + (hi >> (32 - kSliceBucketBits)));
+    // guide entry of Q's bucket; kNarrow: the table's entries are indexed in 32 bits
+    const uint32_t bucket = hi >> (32 - kSliceBucketBits);
+    const uint32_t e = kNarrow
+        ? __ldg(tab.guide + (row * uint32_t(kSliceBuckets) + bucket))
+        : __ldg(tab.guide + ((uint64_t(row) << kSliceBucketBits) + bucket));
     uint32_t count = e & 0x1Fu;
     const uint32_t inside = (e >> 5) & 3u;  // entries in Q's bucket (3: three or more)
     const uint32_t qn = (hi >> (24 - kSliceBucketBits)) & 0xFFu, fn = e >> 8;  // Q bits 54..47
@@ -77,7 +81,7 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
 
 // kMinBlocks counts CTAs of 256 threads (the register bound of the variant
 // table); the kernel runs CTAs of kSliceThreads.
-template <int V, int kMinBlocks, bool kOne>
+template <int V, int kMinBlocks, bool kOne, bool kNarrow>
 __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThreads)
     k_step_slice(PlainArgs p, SliceTables tab)
 {
@@ -146,7 +150,8 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
             }
             b = e0[j];
             if (uint32_t(j) >= nv) a = b = c = 0u;
-            if (slice_node(a, b, c, h ? w2 : w0, h ? w3 : w1, tab, p.C, err)) heavy |= 1u << j;
+            if (slice_node<kNarrow>(a, b, c, h ? w2 : w0, h ? w3 : w1, tab, p.C, err))
+                heavy |= 1u << j;
             om[j] = a;
             o0[j] = b;
             op[j] = c;
@@ -241,8 +246,13 @@ static void launch_slice_v(const PlainArgs &p, bool one, const SliceTables &tab,
 {
     const uint64_t threads = (p.g_end - p.g_begin) * (8u / V);
     const dim3 grid(uint32_t((threads + kSliceThreads - 1) / kSliceThreads));
-    if (one) k_step_slice<V, kMinBlocks, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
-    else k_step_slice<V, kMinBlocks, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    if (tab.guide_narrow) {
+        if (one) k_step_slice<V, kMinBlocks, true, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
+        else k_step_slice<V, kMinBlocks, false, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    } else {
+        if (one) k_step_slice<V, kMinBlocks, true, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
+        else k_step_slice<V, kMinBlocks, false, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    }
 }
 
 // Slice-kernel variants: (nodes per thread, minimum CTAs of 256 threads per
