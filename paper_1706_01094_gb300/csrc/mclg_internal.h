@@ -110,7 +110,7 @@ struct SliceTables {
     uint32_t guide_narrow;          // 1: every guide index fits 32 bits (rows < 2^32 / buckets)
 };
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
-constexpr uint32_t kHeavyBlocks = 304;           // CTAs of the heavy-node pass
+constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass (usually empty)
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
 void build_slice_guide(const uint64_t *F, int n, uint16_t *guide);
 uint32_t slice_variant_vec(uint32_t variant);
