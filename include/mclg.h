@@ -112,12 +112,14 @@ typedef struct {
                                the unsplit batch bit for bit */
     uint32_t sampler;       /* MCLG_SAMPLER_* */
     uint32_t slice_n_max;   /* SLICE: the tables cover node masses N <= slice_n_max (1 ..
-                               4096; 0 = 256); a node with a larger mass takes the
-                               SEQUENTIAL sampler's C decisions (the same bits that sampler
-                               gives it).  The bits depend on slice_n_max like on the seed.
-                               Tables take about 1184 (n+1)^3 / 12 bytes of device memory
-                               (1.7 GB at 256, 13.4 GB at 512); built once, at the first
-                               mclg_step, on the host cores. */
+                               1024; 0 = 256; larger values return MCLG_ERR_ARG); a node
+                               with a larger mass takes the SEQUENTIAL sampler's C
+                               decisions (the same bits that sampler gives it).  The bits
+                               depend on slice_n_max like on the seed.  Tables take about
+                               1184 (n+1)^3 / 12 bytes of device memory and as much host
+                               memory while they are built (1.7 GB at 256, 13.4 GB at 512,
+                               107 GB at 1024, where the 32-bit row index still holds);
+                               built once, at the first mclg_step, on the host cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
                                 mclg_step; v + 1 = use variant v (0 <= v < 6; nodes per thread
                                 and register bound, reported by mclg_tuning).  Every variant
@@ -200,11 +202,15 @@ const char *mclg_status_str(mclg_status s);
  * of it) and loops that cannot accept the device-wide synchronisation that
  * cudaMalloc/cudaFree may imply.  The paper has no counterpart; this is a
  * library convenience.
- *   n       device array, the canonical field n[3][S] (as mclg_get_state writes it)
+ *   n       device array on the current device, the canonical field n[3][S]
+ *           (as mclg_get_state writes it)
  *   S       nodes, 1 <= S <= 2^26 (67,108,864); larger S returns MCLG_ERR_ARG
- *   N, J    device int32 arrays of S entries, or NULL
- *   totals  (sum N, sum J) as two int64, host or device, or NULL; a host
- *           destination synchronises cuda_stream before returning
+ *   N, J    int32 arrays of S entries on the current device, or NULL
+ *   totals  (sum N, sum J) as two int64, host or on the current device, or
+ *           NULL; a host destination synchronises cuda_stream before returning
+ * A buffer on another device (or a host n, N or J) returns MCLG_ERR_ARG before
+ * any launch.  A CUDA error already pending on the calling thread is left in
+ * place and reported as MCLG_ERR_CUDA, with nothing launched.
  * Allocates nothing: its only scratch is a fixed 512 KiB device array that
  * every GPU loading this library holds until the process exits.  The first
  * call on a device looks up that array's device address (with the device
@@ -223,7 +229,9 @@ mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int3
  * min(#{k : F[k] in bucket j}, 3), bits 8-15 bits 54..47 of that F[k] when
  * it is the only one in the bucket (else 0).
  * For checking the tables against an independent computation.  MCLG_ERR_ARG
- * for C > 10 or an invalid state. */
+ * for C > 10, an invalid state, or D = 8 N^2 lambda_den >= 2^44 (the exact
+ * numerators over D^C would not fit the builder's 512-bit integers; with
+ * lambda_den = 1 every N <= 2^20 is accepted, with 256 every N <= 92681). */
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
                            uint16_t *guide);

@@ -1041,9 +1041,11 @@ mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32
 {
     const uint32_t Jp = uint32_t(J < 0 ? -int64_t(J) : J);
     if (!F || !dmin || !dmax || C > uint32_t(kSliceMaxC) || N < 2 || Jp > N || b > N - Jp ||
-        ((N - Jp - b) & 1u) || lambda_den < 1 || lambda_den > 256 || lambda_num > lambda_den ||
-        N > (uint32_t(1) << 20))
+        ((N - Jp - b) & 1u) || lambda_den < 1 || lambda_den > 256 || lambda_num > lambda_den)
         return MCLG_ERR_ARG;
+    // the exact law's numerators over D^C, shifted by 2^64, must fit the
+    // builder's 512-bit integers: D = 8 N^2 lambda_den < 2^44
+    if (8ull * uint64_t(N) * N * lambda_den >= kSliceMaxD) return MCLG_ERR_ARG;
     int lo = 0, hi = 0;
     build_slice_row(N, Jp, b, C, lambda_num, lambda_den, F, lo, hi);
     if (guide) build_slice_guide(F, hi - lo, guide);

@@ -19,7 +19,8 @@ constexpr int kSliceMaxC = 10;                   // slice sampler: sub-collision
 constexpr int kSliceBucketBits = 9;              // guide table: buckets of the top bits of Q
 constexpr int kSliceBuckets = 1 << kSliceBucketBits;
 constexpr int kSliceRowU64 = 20;                 // secondary row: 2C entries
-constexpr uint32_t kSliceMaxN = 4096;            // largest mass the slice tables may cover
+constexpr uint32_t kSliceMaxN = 1024;            // largest mass the slice tables may cover (rows < 2^32)
+constexpr uint64_t kSliceMaxD = uint64_t(1) << 44;  // exact-law denominator base D = 8 N^2 lambda_den
 constexpr uint32_t kSliceDefaultN = 256;         // slice tables' mass range unless set
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
 constexpr uint32_t kSliceVariants = 6;           // slice-kernel launch variants (see launch_slice)

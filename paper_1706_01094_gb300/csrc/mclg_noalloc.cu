@@ -122,14 +122,17 @@ __global__ void __launch_bounds__(kThreads) k_moments_final(long long *__restric
     }
 }
 
-bool on_device(const void *p)
+// The device that holds p, or -1 when p is not device memory (host memory,
+// or an address the runtime does not know).  Managed memory counts as the
+// device it is attributed to.
+int device_of(const void *p)
 {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+        cudaGetLastError();  // clear the lookup failure (entry checked that nothing else was pending)
+        return -1;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
 
 }  // namespace
@@ -139,7 +142,15 @@ extern "C" mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32
 {
     if (!n || S == 0) return MCLG_ERR_ARG;
     if (S > kMaxNodes) return MCLG_ERR_ARG;  // beyond the fixed scratch: 2^26 nodes
-    if (!on_device(n) || (N && !on_device(N)) || (J && !on_device(J))) return MCLG_ERR_ARG;
+    // an error left pending by earlier work of the caller is reported, not consumed
+    if (cudaPeekAtLastError() != cudaSuccess) return MCLG_ERR_CUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MCLG_ERR_CUDA;
+    // every device buffer must live on the current device: the kernels run there
+    if (device_of(n) != dev || (N && device_of(N) != dev) || (J && device_of(J) != dev))
+        return MCLG_ERR_ARG;
+    const int tot_dev = totals ? device_of(totals) : -1;
+    if (tot_dev >= 0 && tot_dev != dev) return MCLG_ERR_ARG;
     long long *scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return MCLG_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -150,8 +161,7 @@ extern "C" mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32
     k_moments_final<<<1, kThreads, 0, s>>>(scratch, blocks);
     if (cudaGetLastError() != cudaSuccess) return MCLG_ERR_CUDA;
     if (totals) {
-        const cudaMemcpyKind kind = on_device(totals) ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyDeviceToHost;
+        const cudaMemcpyKind kind = tot_dev >= 0 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         if (cudaMemcpyAsync(totals, scratch + 2 * kMaxBlocks, 2 * sizeof(long long), kind, s) !=
             cudaSuccess)
             return MCLG_ERR_CUDA;

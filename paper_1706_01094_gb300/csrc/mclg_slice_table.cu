@@ -173,7 +173,7 @@ void build_row(uint32_t N, uint32_t J, uint32_t b, const SliceParams &sp, uint64
     const int64_t bmin = int64_t(N - J) & 1;
     dmin = int(std::max<int64_t>(-C, (bmin - int64_t(b)) / 2));
     dmax = int(std::min<int64_t>(C, (int64_t(N) - J - int64_t(b)) / 2));
-    const uint64_t D = 8ull * N * N * sp.lam_d;
+    const uint64_t D = 8ull * N * N * sp.lam_d;  // < kSliceMaxD (callers check)
     constexpr int W = 2 * kSliceMaxC + 1;
     Big v[W], nv[W], den;
     for (int i = 0; i < W; ++i) big_set(v[i], 0);

@@ -243,12 +243,38 @@ class Lattice:
                 "count": int(cnt[0])}
 
 
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
+
+
+def _dtype_name(a) -> str:
+    return str(a.dtype).replace("torch.", "")
+
+
 def moments_noalloc(n, N=None, J=None, totals=None, stream=None) -> int:
     """mclg_moments_noalloc on a device field n[3, S] (caller-owned buffers).
 
-    For callers that cannot allocate device memory; returns the raw status."""
+    For callers that cannot allocate device memory; returns the raw status.
+    Shapes and dtypes are checked here (ValueError) so that the library never
+    reads or writes past a buffer: n is [3, S] or [3 S] of a 16-bit integer
+    type, N and J int32 with at least S entries, totals int64 with at least 2."""
+    shape = tuple(n.shape)
+    if len(shape) == 2 and shape[0] == 3:
+        S = int(shape[1])
+    elif len(shape) == 1 and shape[0] % 3 == 0:
+        S = int(shape[0]) // 3
+    else:
+        raise ValueError(f"n must be [3, S] or [3 S], got shape {shape}")
+    if _dtype_name(n) not in ("uint16", "int16"):
+        raise ValueError(f"n must hold 16-bit occupations, got {n.dtype}")
+    for name, a in (("N", N), ("J", J)):
+        if a is None:
+            continue
+        if _dtype_name(a) != "int32" or _numel(a) < S:
+            raise ValueError(f"{name} must be int32 with at least {S} entries")
+    if totals is not None and (_dtype_name(totals) != "int64" or _numel(totals) < 2):
+        raise ValueError("totals must be int64 with at least 2 entries")
     lib = load()
-    S = int(n.shape[-1]) if len(n.shape) == 2 else int(n.shape[0]) // 3
     return int(lib.mclg_moments_noalloc(_ptr(n), S, _ptr(N), _ptr(J), _ptr(totals),
                                         _stream_ptr(stream)))
 

@@ -71,3 +71,35 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mclg, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         mclg.Lattice([8])
+
+
+def test_noalloc_binding_refuses_bad_buffers_before_the_library():
+    """Shapes and dtypes that would let mclg_moments_noalloc run past a buffer are
+    refused on the host (no device buffers, no launch)."""
+    import numpy as np
+    from paper_1706_01094_gb300 import mclg
+    n = np.zeros((3, 10), dtype=np.uint16)
+    good_N = np.zeros(10, dtype=np.int32)
+    tot = np.zeros(2, dtype=np.int64)
+    bad = [
+        dict(n=np.zeros((4, 10), dtype=np.uint16)),           # not three planes
+        dict(n=np.zeros(31, dtype=np.uint16)),                # length not a multiple of 3
+        dict(n=np.zeros((3, 10), dtype=np.int32)),            # not 16-bit
+        dict(n=n, N=np.zeros(9, dtype=np.int32)),             # N shorter than S
+        dict(n=n, J=np.zeros(10, dtype=np.int64)),            # J not int32
+        dict(n=n, N=good_N, totals=np.zeros(1, dtype=np.int64)),   # one total slot
+        dict(n=n, totals=np.zeros(2, dtype=np.int32)),        # totals not int64
+    ]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            mclg.moments_noalloc(**kw)
+
+
+def test_noalloc_size_limit_is_checked_first(libpath):
+    """Sizes beyond the fixed scratch are rejected before any CUDA call."""
+    from paper_1706_01094_gb300 import mclg
+    lib = mclg.load()
+    buf = ctypes.create_string_buffer(64)
+    assert lib.mclg_moments_noalloc(buf, (1 << 26) + 1, None, None, None, None) == 1
+    assert lib.mclg_moments_noalloc(buf, 0, None, None, None, None) == 1
+    assert lib.mclg_moments_noalloc(None, 8, None, None, None, None) == 1

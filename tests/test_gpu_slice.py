@@ -79,7 +79,7 @@ def test_nodes_beyond_n_max_take_sequential_draws(variant):
     with pytest.raises(mclg.MCLGError):
         mclg.Lattice(L, sampler=SLICE, C=11)
     with pytest.raises(mclg.MCLGError):
-        mclg.Lattice(L, sampler=SLICE, slice_n_max=4097)
+        mclg.Lattice(L, sampler=SLICE, slice_n_max=1025)
 
 
 def test_slice_full_size_sampled_nodes():

@@ -75,3 +75,23 @@ def test_guide_rows_count_entries_below_each_bucket(lib):
                 hi_q = (j << 55) | ((next8 + 1) << 47)
                 assert oracle.slice_draw(N, J, b, lo_q, C, lam) == b + 2 * (omin + below)
                 assert oracle.slice_draw(N, J, b, hi_q, C, lam) == b + 2 * (omin + below + 1)
+
+
+def test_rows_at_the_largest_accepted_denominators_equal_oracle(lib):
+    """The exact law's numerators over D^C must fit the builder's integers: every
+    (N, lambda_den) the ABI accepts gives the oracle's F (640-bit integers), and
+    D = 8 N^2 lambda_den >= 2^44 is refused instead of returning a wrong row."""
+    cases = [(2**20 - 1, 1), (2**20, 1), (92681, 256), (65535, 256), (46340, 1000 % 257)]
+    for N, ld in cases:
+        assert 8 * N * N * ld < 2**44
+        for J, b in ((0, N - 2 * (N // 3)), (N // 5, (N - N // 5) % 2), (1, N - 1), (N - 2, 2)):
+            for C in (10, 3):
+                lam = (max(1, ld // 2), ld)
+                F, dmin, dmax = lib.slice_row(N, J, b, C, lam)
+                Fo, omin, omax = oracle.slice_cdf(N, J, b, C, lam)
+                assert (dmin, dmax) == (omin, omax)
+                assert [int(v) for v in F] == [int(Fo[dmin + k + C]) for k in range(dmax - dmin)]
+    for N, ld in ((2**20 - 1, 256), (92682, 256), (2**21, 1), (3 * 2**19, 2)):
+        assert 8 * N * N * ld >= 2**44
+        with pytest.raises(lib.MCLGError):
+            lib.slice_row(N, 0, N % 2, 10, (1, ld))
