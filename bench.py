@@ -50,8 +50,13 @@ def int_ops_per_node_step(C: int) -> int:
     return 98 * max(1, -(-C // 10)) + 13 * C
 
 
-INT32_LANES_PER_SM_CLK = 64     # integer pipe lanes per SM and clock
-SMS = 152
+INT32_LANES_PER_SM_CLK = 64     # integer pipe lanes per SM and clock (unit count of the ALU pipe)
+
+
+def sm_count(index: int = 0) -> int:
+    """Streaming multiprocessors of the GPU, from the device attribute."""
+    import torch
+    return int(torch.cuda.get_device_properties(index).multi_processor_count)
 
 
 def parse():
@@ -78,6 +83,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and statistics workloads that the default "
+                         "single-lattice run reports beside its headline")
     return ap.parse_args()
 
 
@@ -108,8 +116,88 @@ def pick_sampler(args) -> str:
     return "slice" if args.workload in ("single", "fluct") else "sequential"
 
 
+class NvmlClocks:
+    """SM clock and clock-event (throttle) reasons read through NVML (libnvidia-ml,
+    read-only queries) from a thread that polls every 0.2 ms, so that even a
+    timed region of a few milliseconds gets samples; one sample is also taken
+    right at its start and right at its end."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        import ctypes
+        self.samples, self.reasons = [], set()
+        self.max_mhz = None
+        self.ok = False
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(cuda_index)
+                bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            except Exception:
+                bus = None
+            rc = 1
+            if bus is not None:
+                rc = self.nvml.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h))
+            if rc != 0:
+                rc = self.nvml.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(self.h))
+            if rc != 0:
+                return
+            mx = ctypes.c_uint(0)
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:  # 1: SM
+                self.max_mhz = float(mx.value)
+            # the reasons query under its current name, or its older one
+            self.why = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def sample(self):
+        import ctypes
+        if not self.ok:
+            return
+        clk, why = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+            self.samples.append(float(clk.value))
+        if self.why is not None and self.why(self.h, ctypes.byref(why)) == 0:
+            for bit, name in self.REASONS.items():
+                if why.value & bit:
+                    self.reasons.add(name)
+
+    def __enter__(self):
+        self._stop = threading.Event()
+        self.sample()
+        self._thread = threading.Thread(target=self._poll, daemon=True)
+        self._thread.start()
+        return self
+
+    def _poll(self):
+        while not self._stop.wait(0.0002):
+            self.sample()
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._thread.join()
+        self.sample()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                    "samples": 0, "source": "nvml"}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples),
+                "min_mhz": min(self.samples), "source": "nvml"}
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region
+    (used when NVML cannot be loaded)."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -198,26 +286,37 @@ def oracle_stepper(sampler: str):
     return oracle.slice_step if sampler == "slice" else oracle.step
 
 
-def oracle_rate(wl, seconds: float, sampler: str):
-    """Time the CPU oracle (single thread, as it stands) for about `seconds` on a
-    bounded sample of the workload; returns (GSUPS, sample description)."""
+def oracle_rate(wl, seconds: float, sampler: str, threads: int = 0):
+    """Time the CPU oracle (as it stands, its node loops on `threads` host cores,
+    0 = all) for about `seconds` on a bounded sample of the workload; returns
+    (GSUPS, sample description, threads used)."""
     import oracle
     ostep = oracle_stepper(sampler)
-    probe = sample_workload(wl, 1 << 12)
+    used = oracle.set_threads(threads)
+    probe = sample_workload(wl, 1 << 14)
     n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
     t0 = time.perf_counter()
     n, err = ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
     rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
-    sw = sample_workload(wl, min(wl.nodes, max(1 << 12, int(rate * seconds / 4))))
+    sw = sample_workload(wl, min(wl.nodes, max(1 << 14, int(rate * seconds / 4))))
     steps = max(1, int(rate * seconds / sw.nodes))
     n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
     assert err == 0
     t0 = time.perf_counter()
     n, err = ostep(sw.L, sw.seed, n, 0, steps, C=sw.C, lam=sw.lam)
     dt = time.perf_counter() - t0
+    oracle.set_threads(0)
     sample = (f"{steps} time step(s) of a {sw.nodes}-node, {sw.replicas}-replica sample of the "
-              f"workload (same profile values), {dt:.1f} s")
-    return sw.nodes * steps / dt / 1e9, sample
+              f"workload (same profile values), {dt:.1f} s on {used} thread(s)")
+    return sw.nodes * steps / dt / 1e9, sample, used
+
+
+def cpu_baseline(wl, seconds: float, sampler: str) -> dict:
+    """The oracle on every host core (the baseline) and on one core beside it."""
+    v, sample, used = oracle_rate(wl, seconds * 2 / 3, sampler, 0)
+    v1, sample1, _ = oracle_rate(wl, seconds / 3, sampler, 1)
+    return {"value": v, "unit": "GSUPS", "cores": used, "kind": "oracle", "sample": sample,
+            "nproc": os.cpu_count(), "single_thread": {"value": v1, "cores": 1, "sample": sample1}}
 
 
 def run_reference(args):
@@ -228,12 +327,14 @@ def run_reference(args):
     import oracle
     sampler_name = pick_sampler(args)
     ostep = oracle_stepper(sampler_name)
+    cores = oracle.set_threads(0)  # the oracle's node loops on every host core
     # size the per-step sample so that warm-up + timed steps take about two minutes
-    probe = sample_workload(wl, 1 << 12)
+    probe = sample_workload(wl, 1 << 14)
     n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
-    t0 = time.perf_counter()
-    ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
-    rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
+    for k in range(2):  # the second pass times the oracle with the laws it remembers
+        t0 = time.perf_counter()
+        ostep(probe.L, probe.seed, n, k, 1, C=probe.C, lam=probe.lam)
+        rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
     per_step = 120.0 / max(1, args.steps + args.warmup)
     sw = sample_workload(wl, max(8, int(rate * per_step)))  # one 8-node chunk at least
     n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
@@ -256,8 +357,8 @@ def run_reference(args):
             "scaling": "weak" if wl.replicas == 1 else "strong",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": {**config_dict(wl, args, world), "sampler": sampler_name},
-            "cpu_baseline": {"value": value, "unit": "GSUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GSUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample, "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": "GSUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -316,6 +417,94 @@ def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=Fa
     return graph_launches(steps, 1)
 
 
+def stats_report(lat, wl) -> dict:
+    """FP32-vs-FP64 error of the statistics and their Poisson check (Eqs. poisson,
+    corr): pooled mean and variance over f^eq of Eq. D1Q3equil."""
+    import math
+    st = lat.stats_read()
+    rho, u = float(wl.rho[0]), float(wl.u[0])
+    sq = math.sqrt(1.0 + 3.0 * u * u) - 1.0
+    feq = np.array([rho * w * (1 + 3 * v * u + (3 * v * v - 1) * sq)
+                    for w, v in ((1 / 6, -1), (2 / 3, 0), (1 / 6, 1))])
+    var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
+    var64 = st["cov64"][:, [0, 3, 5]]
+    scale = np.sqrt(var64[:, [0, 0, 1]] * var64[:, [1, 2, 2]])
+    cnt = st["count"]
+    mean = st["s1"].sum(axis=0) / (float(cnt) * float(wl.L[0]))  # no uint32 product
+    return {
+        "samples_per_position": cnt,
+        "fp32_var_max_rel_err_vs_fp64": float((np.abs(var32 - var64) / var64).max()),
+        "fp32_cov_max_err_rel_sqrt_var": float((np.abs(st["cov32"][:, [1, 2, 4]]
+                                                       - st["cov64"][:, [1, 2, 4]]) / scale).max()),
+        "target_rel_err": 1e-6,
+        "mean_over_feq": (mean / feq).tolist(),
+        "var_over_feq_pooled": (var64.mean(axis=0) / feq).tolist(),
+        "feq": feq.tolist(),
+    }
+
+
+def timed_steps(lat, stream, steps: int) -> float:
+    """Milliseconds of one mclg_step(steps) call, CUDA events on the handle's stream."""
+    import torch
+    lat.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    lat.sync()
+    return e0.elapsed_time(e1)
+
+
+def batched_extra(mclg, persistent_steps: int = 2000, plain_steps: int = 10) -> dict:
+    """The 4096 x 1024 batch (rho ~ U[5, 500], u ~ U[-0.3, 0.3]): one persistent
+    launch for all its steps against one plain-kernel launch per replica and step
+    (the per-replica baseline, timed on fewer steps: it is launch-bound)."""
+    import torch
+    wl = workloads.batched()
+    out = {"workload": f"batched: {wl.replicas} replicas x {int(wl.L[0])} nodes, C={wl.C}, "
+                       "rho ~ U[5,500], u ~ U[-0.3,0.3]", "sampler": "sequential"}
+    stream = torch.cuda.Stream()
+    for name, mode, steps in (("persistent", mclg.MODE_PERSISTENT, persistent_steps),
+                              ("per_replica_plain", mclg.MODE_PLAIN, plain_steps)):
+        with mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode,
+                          stream=stream) as lat:
+            lat.init(wl.rho, wl.u)
+            tot0 = lat.totals()
+            lat.step(2)  # autotuning and warm-up
+            ms = timed_steps(lat, stream, steps)
+            assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
+            out[name] = {"gsups": wl.nodes * steps / (ms / 1e3) / 1e9, "steps": steps,
+                         "ms_per_step": ms / steps,
+                         "launches_per_step": (1.0 / steps if mode == mclg.MODE_PERSISTENT
+                                               else wl.replicas)}
+            if mode == mclg.MODE_PERSISTENT:
+                out["tuning"] = lat.tuning()
+    out["speedup"] = out["persistent"]["gsups"] / out["per_replica_plain"]["gsups"]
+    return out
+
+
+def stats_extra(mclg, burn_in: int = 1000, steps: int = 10_000) -> list:
+    """The fluctuation workload (512 x 4096, rho = 50, u in {0, 0.2}): 10^4 steps of
+    statistics after 10^3 burn-in, slice sampler; GSUPS and the FP32 error."""
+    import torch
+    out = []
+    stream = torch.cuda.Stream()
+    for u in (0.0, 0.2):
+        wl = workloads.fluct(u=u)
+        with mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, flags=mclg.STATS,
+                          sampler=mclg.SAMPLER_SLICE, stream=stream) as lat:
+            lat.init(wl.rho, wl.u)
+            lat.step(burn_in)
+            lat.stats_reset()
+            ms = timed_steps(lat, stream, steps)
+            rep = stats_report(lat, wl)
+        out.append({"u": u, "gsups": wl.nodes * steps / (ms / 1e3) / 1e9, "steps": steps,
+                    "burn_in": burn_in, **rep})
+    return out
+
+
 def run_gb300(args):
     import torch
     rank, world, local = dist_env()
@@ -358,7 +547,10 @@ def run_gb300(args):
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
+    clocks = NvmlClocks(local)
+    if not clocks.ok:
+        clocks = ClockSampler(local)
+    with clocks:
         ev0.record(stream)
         persistent = (mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)) \
             and not stats_on and sampler != mclg.SAMPLER_SLICE
@@ -381,28 +573,7 @@ def run_gb300(args):
     value = nodes_all * args.steps / (t_max / 1e3) / 1e9
     launches = count_launches(args.steps, wl, mode, persistent, stats_on, mclg,
                               sampler == mclg.SAMPLER_SLICE)
-    stats_summary = None
-    if stats_on:
-        st = lat.stats_read()
-        import math
-        rho, u = float(wl.rho[0]), float(wl.u[0])
-        sq = math.sqrt(1.0 + 3.0 * u * u) - 1.0
-        feq = np.array([rho * w * (1 + 3 * v * u + (3 * v * v - 1) * sq)
-                        for w, v in ((1 / 6, -1), (2 / 3, 0), (1 / 6, 1))])
-        var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
-        var64 = st["cov64"][:, [0, 3, 5]]
-        scale = np.sqrt(var64[:, [0, 0, 1]] * var64[:, [1, 2, 2]])
-        cnt = st["count"]
-        mean = st["s1"].sum(axis=0) / (float(cnt) * float(wl.L[0]))  # no uint32 product
-        stats_summary = {
-            "samples_per_position": cnt,
-            "fp32_var_max_rel_err_vs_fp64": float((np.abs(var32 - var64) / var64).max()),
-            "fp32_cov_max_err_rel_sqrt_var": float((np.abs(st["cov32"][:, [1, 2, 4]]
-                                                           - st["cov64"][:, [1, 2, 4]]) / scale).max()),
-            "mean_over_feq": (mean / feq).tolist(),
-            "var_over_feq_pooled": (var64.mean(axis=0) / feq).tolist(),
-            "feq": feq.tolist(),
-        }
+    stats_summary = stats_report(lat, wl) if stats_on else None
 
     # end to end through the C ABI with pinned host buffers: every step uploads
     # the state, advances one step and reads the new state back
@@ -435,7 +606,8 @@ def run_gb300(args):
         clk = clocks.summary()
         ms_launch = ms / max(1, launches) if launches else ms
         per_launch_nodes = wl.nodes if args.mode != "plain" or wl.replicas == 1 else None
-        alu_peak = INT32_LANES_PER_SM_CLK * SMS * sm_max * 1e6 / 1e9  # Gop/s
+        sms = sm_count(local)
+        alu_peak = INT32_LANES_PER_SM_CLK * sms * sm_max * 1e6 / 1e9  # Gop/s
         achieved_gbs = BYTES_PER_NODE_STEP * wl.nodes * args.steps / (ms / 1e3) / 1e9
         hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                "frac": achieved_gbs / hbm_peak, "bytes_per_node_step": BYTES_PER_NODE_STEP,
@@ -450,15 +622,25 @@ def run_gb300(args):
                                                                  "issue_active_pct"),
                         "time_basis": "whole step (table kernel + heavy-node pass) per step"}
         else:
+            # integer-bound: the fraction is ncu's ALU-pipe utilisation of the kernel on
+            # this workload (committed profile); the hand tally of integer operations
+            # against the unit-count peak is kept beside it
             achieved_ops = int_ops_per_node_step(wl.C) * wl.nodes * args.steps / (ms / 1e3) / 1e9
             kernel = ("k_step_plain" if (wl.replicas == 1 or args.mode in ("plain", "batched"))
                       else "k_step_persistent")
-            roofline = {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
-                        "unit": "Gop/s", "frac": achieved_ops / alu_peak,
+            alu_pct = committed_figure(kernel, wl.name, "alu_pipe_pct")
+            roofline = {"bound": "alu", "achieved": alu_pct, "peak": 100.0,
+                        "unit": "% of ALU-pipe issue (ncu sm__inst_executed_pipe_alu)",
+                        "frac": None if alu_pct is None else alu_pct / 100.0,
+                        "issue_active_pct_ncu": committed_figure(kernel, wl.name,
+                                                                 "issue_active_pct"),
                         "traffic": committed_figure(kernel, wl.name), "kernel": kernel,
-                        "ops_per_node_step": int_ops_per_node_step(wl.C),
-                        "peak_basis": (f"{INT32_LANES_PER_SM_CLK} int32 lanes x {SMS} SMs x "
-                                       f"{sm_max:.0f} MHz"),
+                        "op_tally": {"ops_per_node_step": int_ops_per_node_step(wl.C),
+                                     "achieved_gops": achieved_ops, "peak_gops": alu_peak,
+                                     "frac": achieved_ops / alu_peak,
+                                     "peak_basis": (f"{INT32_LANES_PER_SM_CLK} int32 lanes x "
+                                                    f"{sms} SMs (device attribute) x "
+                                                    f"{sm_max:.0f} MHz")},
                         "hbm": hbm}
         line = {
             "metric": metric(wl.C), "value": value, "unit": "GSUPS", "n_gpus": world,
@@ -479,10 +661,12 @@ def run_gb300(args):
             "ms_per_launch": ms_launch,
             "clocks": clk,
         }
+        line["config"]["sms"] = sms
+        if world == 1 and args.workload == "single" and not args.no_extras:
+            line["batched"] = batched_extra(mclg)
+            line["stats"] = stats_extra(mclg)
         if world == 1 and not args.no_cpu_baseline:
-            v, sample = oracle_rate(wl, args.cpu_seconds, sampler_name)
-            line["cpu_baseline"] = {"value": v, "unit": "GSUPS", "cores": 1, "kind": "oracle",
-                                    "sample": sample}
+            line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, sampler_name)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -7,7 +7,8 @@ the library: the two share nothing but the seeded workload generators.
 
 ``mclg_oracle.c`` holds the slow, plain reference (Philox4x32-10, the exact
 sub-collision sampler, streaming, Poisson initialisation, moments, exact
-statistics); this module builds it with gcc and wraps it with ctypes.
+statistics); this module builds it with gcc (OpenMP over the nodes of a step,
+which does not change any result) and wraps it with ctypes.
 ``exact.py`` holds rational-arithmetic tools (enumeration of the paper's
 particle picks, stationary laws) used to pin it.
 """
@@ -39,8 +40,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-             "-shared", "-o", tmp, _SRC, "-lm"])
+            ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+             "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -78,8 +79,22 @@ def _load():
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
             lib.orc_exact_cov.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, u64]
             lib.orc_exact_cov.restype = ctypes.c_double
+            lib.orc_set_threads.argtypes = [i32]
+            lib.orc_set_threads.restype = i32
+            lib.orc_threads.argtypes = []
+            lib.orc_threads.restype = i32
             _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's node loops (0: every core); returns the count in use.
+    Results do not depend on it: every node writes only its own entries."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def threads() -> int:
+    return int(_load().orc_threads())
 
 
 def _ptr(a: np.ndarray):

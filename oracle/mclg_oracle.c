@@ -14,6 +14,13 @@
  * initialisation.  Build with -ffp-contract=off (no fused multiply-add) so the
  * FP64 initialisation is reproducible.
  *
+ * The node loops of one time step (and of the initialisation) are shared out
+ * over the host cores with OpenMP when it is available: every node reads the
+ * field of the previous step and writes only its own entries, so the results
+ * do not depend on the number of threads.  The slice sampler's exact laws are
+ * remembered in a table keyed by their arguments (caching only: each law is
+ * still computed by the plain big-integer recursion below the first time).
+ *
  * State layout used by every function here: n[3 * S] uint16, S = sum of the
  * replica lengths L[r]; plane i (0, 1, 2) holds the particles with velocity
  * v = i - 1 (-1, 0, +1); replica r occupies nodes [off_r, off_r + L[r]) of
@@ -43,6 +50,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_ERR_OVERFLOW 1u /* a transition would leave [0, 65535] */
 #define ORC_ERR_SAMPLER 2u  /* decision still open after the refinement cap */
@@ -88,6 +98,27 @@ static void seed_key(uint64_t seed, uint32_t key[2])
 {
     key[0] = (uint32_t)seed;
     key[1] = (uint32_t)(seed >> 32);
+}
+
+/* Threads of the node loops (1 without OpenMP); n <= 0 selects every core. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* The 128-bit value of one Philox block, word 0 least significant. */
@@ -150,9 +181,13 @@ int orc_init(const uint32_t *L, uint32_t R, uint64_t seed, const double *rho, co
     int err = 0;
     uint64_t off = 0;
     for (uint32_t r = 0; r < R; r++) {
+#pragma omp parallel for schedule(static) reduction(| : err)
         for (uint32_t x = 0; x < L[r]; x++) {
             double rh = rho[off + x], uu = u[off + x];
-            if (!(rh >= 0.0) || !isfinite(rh) || !(fabs(uu) <= 1.0)) return 8;
+            if (!(rh >= 0.0) || !isfinite(rh) || !(fabs(uu) <= 1.0)) {
+                err |= 8;
+                continue;
+            }
             double f[3];
             orc_feq(rh, uu, f);
             for (uint32_t i = 0; i < 3; i++) {
@@ -179,7 +214,7 @@ int orc_init(const uint32_t *L, uint32_t R, uint64_t seed, const double *rho, co
         }
         off += L[r];
     }
-    return err;
+    return (err & 8) ? 8 : err;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -325,6 +360,7 @@ static void stream(const uint32_t *L, uint32_t R, uint64_t S, const uint16_t *po
     uint64_t off = 0;
     for (uint32_t r = 0; r < R; r++) {
         uint32_t Lr = L[r];
+#pragma omp parallel for schedule(static) if (Lr >= 65536)
         for (uint32_t x = 0; x < Lr; x++) {
             for (int i = 0; i < 3; i++) {
                 int v = i - 1;
@@ -385,17 +421,21 @@ int orc_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uint32_t 
     int err = 0;
     for (uint64_t s = 0; s < n_steps; s++) {
         uint32_t t = (uint32_t)(t0 + s);
-        uint64_t off = 0;
-        for (uint32_t r = 0; r < R; r++) {
-            for (uint32_t x = 0; x < L[r]; x++) {
-                uint16_t st[3] = {n[0 * S + off + x], n[1 * S + off + x], n[2 * S + off + x]};
-                uint32_t ln, ld;
-                node_lambda(flags, (uint32_t)st[0] + st[1] + st[2], (int32_t)st[2] - (int32_t)st[0],
-                            lam_n, lam_d, &ln, &ld);
-                err |= collide_node(st, x, r0 + r, t, C, ln, ld, key);
-                for (int i = 0; i < 3; i++) post[i * S + off + x] = st[i];
+#pragma omp parallel reduction(| : err)
+        {
+            uint64_t off = 0;
+            for (uint32_t r = 0; r < R; r++) {
+#pragma omp for schedule(static) nowait
+                for (uint32_t x = 0; x < L[r]; x++) {
+                    uint16_t st[3] = {n[0 * S + off + x], n[1 * S + off + x], n[2 * S + off + x]};
+                    uint32_t ln, ld;
+                    node_lambda(flags, (uint32_t)st[0] + st[1] + st[2],
+                                (int32_t)st[2] - (int32_t)st[0], lam_n, lam_d, &ln, &ld);
+                    err |= collide_node(st, x, r0 + r, t, C, ln, ld, key);
+                    for (int i = 0; i < 3; i++) post[i * S + off + x] = st[i];
+                }
+                off += L[r];
             }
-            off += L[r];
         }
         if (flags & ORC_FLAG_NO_STREAM)
             memcpy(n, post, 3 * S * sizeof(uint16_t));
@@ -676,8 +716,8 @@ static void slice_thresholds(int64_t N, int64_t J, int64_t b, uint32_t lam_n, ui
 
 /* F[d + C] = floor(CDF[d] 2^64) for d in [-C, C] and the reachable offsets
  * [*dmin, *dmax].  Returns 0, or -1 for C > SLICE_MAX_C. */
-int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
-                  uint64_t *F, int32_t *dmin, int32_t *dmax)
+static int slice_cdf_compute(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n,
+                             uint32_t lam_d, uint64_t *F, int32_t *dmin, int32_t *dmax)
 {
     if (C > SLICE_MAX_C) return -1;
     const int W = 2 * SLICE_MAX_C + 1;
@@ -731,6 +771,81 @@ int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n,
     return 0;
 }
 
+/* Remembered laws: an open-addressing table keyed by every argument of the
+ * law, filled under a lock, read without one (a slot's key and values are
+ * written before its state is published, and never change afterwards).  A
+ * reader that meets an empty slot computes the law itself; when the table is
+ * 3/4 full, new laws are computed but no longer remembered. */
+#define CDF_SLOTS (1u << 19)
+typedef struct {
+    uint32_t ready; /* 0 empty, 1 published (atomic, release/acquire) */
+    uint32_t N, b, C, lam_n, lam_d;
+    int32_t J, dmin, dmax;
+    uint64_t F[2 * SLICE_MAX_C + 1];
+} cdf_slot;
+static cdf_slot *cdf_table = NULL;
+static uint32_t cdf_used = 0;
+
+static uint32_t cdf_hash(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n,
+                         uint32_t lam_d)
+{
+    uint64_t h = 1469598103934665603ull; /* FNV-1a over the six arguments */
+    uint32_t k[6] = {N, (uint32_t)J, b, C, lam_n, lam_d};
+    for (int i = 0; i < 6; i++) {
+        h ^= k[i];
+        h *= 1099511628211ull;
+    }
+    return (uint32_t)(h ^ (h >> 32)) & (CDF_SLOTS - 1);
+}
+
+static int cdf_match(const cdf_slot *e, uint32_t N, int32_t J, uint32_t b, uint32_t C,
+                     uint32_t lam_n, uint32_t lam_d)
+{
+    return e->N == N && e->J == J && e->b == b && e->C == C && e->lam_n == lam_n &&
+           e->lam_d == lam_d;
+}
+
+int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
+                  uint64_t *F, int32_t *dmin, int32_t *dmax)
+{
+    if (C > SLICE_MAX_C) return -1;
+    cdf_slot *table = __atomic_load_n(&cdf_table, __ATOMIC_ACQUIRE);
+    uint32_t h = cdf_hash(N, J, b, C, lam_n, lam_d);
+    if (table) {
+        for (uint32_t i = h;; i = (i + 1) & (CDF_SLOTS - 1)) {
+            const cdf_slot *e = &table[i];
+            if (!__atomic_load_n(&e->ready, __ATOMIC_ACQUIRE)) break;
+            if (cdf_match(e, N, J, b, C, lam_n, lam_d)) {
+                memcpy(F, e->F, (2 * C + 1) * sizeof(uint64_t));
+                *dmin = e->dmin;
+                *dmax = e->dmax;
+                return 0;
+            }
+        }
+    }
+    int rc = slice_cdf_compute(N, J, b, C, lam_n, lam_d, F, dmin, dmax);
+#pragma omp critical(orc_cdf_table)
+    {
+        if (!cdf_table) __atomic_store_n(&cdf_table, (cdf_slot *)calloc(CDF_SLOTS, sizeof(cdf_slot)),
+                                         __ATOMIC_RELEASE);
+        if (cdf_table && cdf_used < CDF_SLOTS / 4 * 3) {
+            uint32_t i = h;
+            while (cdf_table[i].ready && !cdf_match(&cdf_table[i], N, J, b, C, lam_n, lam_d))
+                i = (i + 1) & (CDF_SLOTS - 1);
+            cdf_slot *e = &cdf_table[i];
+            if (!e->ready) {
+                e->N = N; e->J = J; e->b = b; e->C = C; e->lam_n = lam_n; e->lam_d = lam_d;
+                e->dmin = *dmin;
+                e->dmax = *dmax;
+                memcpy(e->F, F, (2 * C + 1) * sizeof(uint64_t));
+                __atomic_store_n(&e->ready, 1u, __ATOMIC_RELEASE);
+                cdf_used++;
+            }
+        }
+    }
+    return rc;
+}
+
 /* The 64-bit uniform prefix Q of node x of replica r at time t (the
  * contract above). */
 uint64_t orc_slice_q(uint32_t x, uint32_t r, uint32_t t, const uint32_t key[2])
@@ -771,8 +886,11 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
     int err = 0;
     for (uint64_t s = 0; s < n_steps; s++) {
         uint32_t t = (uint32_t)(t0 + s);
+#pragma omp parallel reduction(| : err)
+        {
         uint64_t off = 0;
         for (uint32_t r = 0; r < R; r++) {
+#pragma omp for schedule(static) nowait
             for (uint32_t x = 0; x < L[r]; x++) {
                 uint32_t a = n[off + x], b = n[S + off + x], c = n[2 * S + off + x];
                 uint32_t N = a + b + c;
@@ -802,6 +920,7 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
                 post[2 * S + off + x] = (uint16_t)c;
             }
             off += L[r];
+        }
         }
         if (flags & ORC_FLAG_NO_STREAM)
             memcpy(n, post, 3 * S * sizeof(uint16_t));

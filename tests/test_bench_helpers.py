@@ -70,3 +70,25 @@ def test_op_tally_and_metric_follow_C():
     args = types.SimpleNamespace(u=0.2, C=1)
     assert bench.make_workload("single", args).C == 1
     assert bench.make_workload("fluct", types.SimpleNamespace(u=0.0, C=10)).C == 10
+
+
+def test_clock_samplers_fail_soft_without_a_gpu():
+    """Without NVML or a GPU the NVML sampler reports itself unusable (the bench
+    then falls back to nvidia-smi polling); with no samples the summary says so."""
+    c = bench.NvmlClocks(0)
+    if not c.ok:
+        with c:
+            pass
+        s = c.summary()
+        assert s["samples"] == 0 and s["sm_mhz"] is None
+    smi = bench.ClockSampler(0)
+    assert smi.summary()["samples"] == 0
+
+
+def test_cpu_baseline_reports_all_cores_and_one():
+    wl = workloads.small()
+    cb = bench.cpu_baseline(wl, 0.6, "sequential")
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    import oracle
+    assert cb["cores"] == oracle.set_threads(0)

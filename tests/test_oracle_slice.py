@@ -151,3 +151,31 @@ def test_slice_uniform_bits_are_uniform_and_independent():
     top = (qs >> np.uint64(56)).astype(np.float64)
     assert abs(np.corrcoef(top[:-1], top[1:])[0, 1]) < 0.04
     assert len(set(int(q) for q in qs)) == len(qs)
+
+
+def test_results_do_not_depend_on_thread_count_or_remembered_laws():
+    """The node loops run on several host threads and the exact laws are
+    remembered between calls: neither may change a single bit.  One thread with
+    laws computed afresh (distinct lambda keys, so nothing is remembered yet)
+    against all threads with laws remembered from the first pass."""
+    from paper_1706_01094_gb300 import workloads
+    L = np.array([3000, 17, 65536 + 9, 64], dtype=np.uint32)
+    n0 = workloads.random_state(L, 60.0, seed=44)
+    results = []
+    for threads in (1, 0, 3):
+        oracle.set_threads(threads)
+        a, ea = oracle.step(L, 5, n0, 2, 3, lam=(5, 7))
+        b, eb = oracle.slice_step(L, 5, n0, 2, 3, lam=(5, 7), n_max=80)
+        rho = np.full(int(L.sum()), 37.5)
+        u = np.linspace(-0.3, 0.3, int(L.sum()))
+        c, ec = oracle.init(L, 9, rho, u)
+        results.append((a, b, c, ea, eb, ec))
+    oracle.set_threads(0)
+    for other in results[1:]:
+        for x, y in zip(results[0], other):
+            assert np.array_equal(x, y)
+    # a remembered law equals the same law computed with C changed and back
+    F1 = oracle.slice_cdf(77, -5, 30, 10, (5, 7))
+    oracle.slice_cdf(77, -5, 30, 9, (5, 7))
+    F2 = oracle.slice_cdf(77, -5, 30, 10, (5, 7))
+    assert np.array_equal(F1[0], F2[0]) and F1[1:] == F2[1:]
