@@ -293,11 +293,12 @@ def oracle_rate(wl, seconds: float, sampler: str, threads: int = 0):
     import oracle
     ostep = oracle_stepper(sampler)
     used = oracle.set_threads(threads)
-    probe = sample_workload(wl, 1 << 14)
+    probe = sample_workload(wl, 1 << 16)
     n, err = oracle.init(probe.L, probe.seed, probe.rho, probe.u)
-    t0 = time.perf_counter()
-    n, err = ostep(probe.L, probe.seed, n, 0, 1, C=probe.C, lam=probe.lam)
-    rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
+    for k in range(2):  # the second pass times the oracle with the laws it remembers
+        t0 = time.perf_counter()
+        ostep(probe.L, probe.seed, n, k, 1, C=probe.C, lam=probe.lam)
+        rate = probe.nodes / max(time.perf_counter() - t0, 1e-9)
     sw = sample_workload(wl, min(wl.nodes, max(1 << 14, int(rate * seconds / 4))))
     steps = max(1, int(rate * seconds / sw.nodes))
     n, err = oracle.init(sw.L, sw.seed, sw.rho, sw.u)
