@@ -62,7 +62,8 @@ typedef enum {
     MCLG_ERR_NOMEM = 2,    /* device or host allocation failed */
     MCLG_ERR_CUDA = 3,     /* a CUDA runtime call failed */
     MCLG_ERR_OVERFLOW = 4, /* an occupation would leave [0, 65535]; state unspecified */
-    MCLG_ERR_TIMEOUT = 5,  /* reserved: a bounded device-side wait gave up */
+    MCLG_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up (the warp-specialised
+                              slice kernel's pipeline waits, about 2 s each); state unspecified */
     MCLG_ERR_STATE = 6,    /* no state yet (call mclg_init or mclg_set_state) */
     MCLG_ERR_SAMPLER = 7   /* a decision stayed open (sequential: after 4 refinement chunks,
                               p < 2^-70; slice: the 64-bit prefix hit a table value, p < 2^-59) */
@@ -121,9 +122,12 @@ typedef struct {
                                107 GB at 1024, where the 32-bit row index still holds);
                                built once, at the first mclg_step, on the host cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
-                                mclg_step; v + 1 = use variant v (0 <= v < 6; nodes per thread
-                                and register bound, reported by mclg_tuning).  Every variant
-                                gives the same bits; this only fixes the launch shape. */
+                                mclg_step; v + 1 = use variant v (SEQUENTIAL: 0 <= v < 6, nodes
+                                per thread and register bound; SLICE: 0 <= v < 10, 0-5 likewise,
+                                6-9 the warp-specialised form with bulk-copy staging, which
+                                applies to single-replica launches; reported by mclg_tuning).
+                                Every variant gives the same bits; this only fixes the launch
+                                shape. */
 } mclg_params;
 
 /* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0,

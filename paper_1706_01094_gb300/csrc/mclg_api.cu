@@ -101,6 +101,7 @@ mclg_status status_from_bits(uint32_t bits)
 {
     if (bits & kErrOverflow) return MCLG_ERR_OVERFLOW;
     if (bits & kErrSampler) return MCLG_ERR_SAMPLER;
+    if (bits & kErrTimeout) return MCLG_ERR_TIMEOUT;
     return MCLG_OK;
 }
 

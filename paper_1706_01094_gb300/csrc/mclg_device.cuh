@@ -1,6 +1,8 @@
 // Device building blocks of the D1Q3 MCLG step: Philox4x32-10 in registers and
 // the exact integer sampler of one sub-collision (Sec. III, Sec. III.A).
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 #ifndef MCLG_HD
@@ -18,6 +20,7 @@ constexpr int kMaxRefine = 4;        // 16-bit refinement chunks allowed per dec
 
 constexpr uint32_t kErrOverflow = 1u;
 constexpr uint32_t kErrSampler = 2u;
+constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait gave up
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds; each multiplies words 0 and
 // 2 by the two round constants, swaps the halves and xors in the round key;
@@ -44,9 +47,10 @@ MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x
 }
 
 // The ten round keys of Philox4x32-10 for one seed, precomputed once per launch
-// (they are the same for every counter).
+// (they are the same for every counter); the two words of a round side by
+// side, so that a kernel reads a round's keys with one 8-byte load.
 struct RoundKeys {
-    uint32_t k0[10], k1[10];
+    uint2 k[10];  // .x: key word 0, .y: key word 1 of round i
 };
 
 MCLG_HD RoundKeys make_round_keys(uint64_t seed)
@@ -54,8 +58,8 @@ MCLG_HD RoundKeys make_round_keys(uint64_t seed)
     RoundKeys rk;
     uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
     for (int i = 0; i < 10; ++i) {
-        rk.k0[i] = k0;
-        rk.k1[i] = k1;
+        rk.k[i].x = k0;
+        rk.k[i].y = k1;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -69,8 +73,8 @@ MCLG_HD void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
         const uint64_t p0 = uint64_t(0xD2511F53u) * x0, p1 = uint64_t(0xCD9E8D57u) * x2;
-        const uint32_t y0 = uint32_t(p1 >> 32) ^ x1 ^ rk.k0[round];
-        const uint32_t y2 = uint32_t(p0 >> 32) ^ x3 ^ rk.k1[round];
+        const uint32_t y0 = uint32_t(p1 >> 32) ^ x1 ^ rk.k[round].x;
+        const uint32_t y2 = uint32_t(p0 >> 32) ^ x3 ^ rk.k[round].y;
         x1 = uint32_t(p1);
         x3 = uint32_t(p0);
         x0 = y0;

@@ -23,7 +23,8 @@ constexpr uint32_t kSliceMaxN = 1024;            // largest mass the slice table
 constexpr uint64_t kSliceMaxD = uint64_t(1) << 44;  // exact-law denominator base D = 8 N^2 lambda_den
 constexpr uint32_t kSliceDefaultN = 256;         // slice tables' mass range unless set
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
-constexpr uint32_t kSliceVariants = 6;           // slice-kernel launch variants (see launch_slice)
+constexpr uint32_t kSliceVariants = 10;          // slice-kernel launch variants (see launch_slice)
+constexpr uint32_t kSliceClassicVariants = 6;    // of which k_step_slice; the rest k_step_slice_ws
 
 // Device-resident description of the internal replica order.
 struct Layout {

@@ -27,7 +27,9 @@
 // so exactly the heavy nodes have N > n_max after the table kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "mclg_device.cuh"
 #include "mclg_internal.h"
@@ -45,7 +47,7 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
     if (N < 2u) return false;
     if (N > tab.n_max) return true;
     const uint32_t Jp = a > c ? a - c : c - a;
-    const uint32_t below = (b - ((N - Jp) & 1u)) >> 1;
+    const uint32_t below = b >> 1;  // the state's row within its slice (b has the parity of N - |J|)
     const uint32_t row = __ldg(tab.rowstart + N * (tab.n_max + 1u) + Jp) + below;
     // guide entry of Q's bucket; kNarrow: the table's entries are indexed in 32 bits
     const uint32_t bucket = hi >> (32 - kSliceBucketBits);
@@ -79,26 +81,207 @@ __device__ __forceinline__ bool slice_node(uint32_t &a, uint32_t &b, uint32_t &c
     return false;
 }
 
+// The exact finish of a draw whose guide entry leaves Q undecided: compare Q
+// with the row's u64 values from `count` on.  Returns the final count; sets
+// the sampler error bit on a tie.
+__device__ __noinline__ uint32_t slice_finish(uint32_t count, uint32_t nvalid, uint64_t Q,
+                                              const unsigned long long *F, uint32_t &err)
+{
+    uint64_t f = 0;
+    while (count < nvalid && (f = __ldg(F + count)) < Q) ++count;
+    if (count < nvalid && f == Q) err |= kErrSampler;
+    return count;
+}
+
+// The table draws of one thread's V consecutive nodes [x0, x0 + V) of a
+// replica (nv of them valid, the rest padding that stays empty), from the
+// streamed planes em, e0, ep (device form) and the two halo values: nxt =
+// B_-1(x0 + V) and prv = B_+1(x0 - 1), periodic.  Writes the post-collision
+// values; returns a bit per node left for the heavy-node pass.  Node by node
+// (slice_node), one Philox block per node pair.
+template <int V, bool kNarrow>
+__device__ __forceinline__ uint32_t slice_vector(const uint32_t (&em)[V], const uint32_t (&e0)[V],
+                                                 const uint32_t (&ep)[V], uint32_t nxt,
+                                                 uint32_t prv, bool stream, uint32_t x0,
+                                                 uint32_t nv, uint32_t r, uint32_t t,
+                                                 const PlainArgs &p, const SliceTables &tab,
+                                                 uint32_t (&om)[V], uint32_t (&o0)[V],
+                                                 uint32_t (&op)[V], uint32_t &err)
+{
+    uint32_t heavy = 0;
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) {
+        uint32_t w0 = (x0 >> 1) + uint32_t(i), w1 = r, w2 = t, w3 = kPurposeSlice << 28;
+        philox4x32_10(w0, w1, w2, w3, p.rk);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * i + h;
+            // pre-collision occupations n_i(x) = B_i(x - v_i); padding stays empty
+            uint32_t a, b, c;
+            if (stream) {
+                a = (uint32_t(j) + 1u < nv) ? em[(j + 1) % V] : nxt;
+                c = (j > 0) ? ep[(j + V - 1) % V] : prv;
+            } else {
+                a = em[j];
+                c = ep[j];
+            }
+            b = e0[j];
+            if (uint32_t(j) >= nv) a = b = c = 0u;
+            if (slice_node<kNarrow>(a, b, c, h ? w2 : w0, h ? w3 : w1, tab, p.C, err))
+                heavy |= 1u << j;
+            om[j] = a;
+            o0[j] = b;
+            op[j] = c;
+        }
+    }
+    return heavy;
+}
+
+// The same draws as slice_vector, with the work in phases over all V nodes so
+// that each thread has V table loads in flight at once: the row starts of
+// every node, the Philox blocks (while those loads are out), the guide
+// entries, then a branch-free decoding; the rare draws that the guide leaves
+// open are finished on the u64 values afterwards, in one branch per thread.
+// Nodes with N < 2 or beyond the tables load nothing and keep their state.
+//
+// `inputs_used` runs once the row-start loads, whose addresses depend on every
+// input value (the halo values included), have been issued: by then the
+// inputs have arrived in registers, so their shared-memory stage can be
+// handed back.
+template <int V, bool kNarrow, typename InputsUsed>
+__device__ __forceinline__ uint32_t slice_vector_phased(
+    const uint32_t (&em)[V], const uint32_t (&e0)[V], const uint32_t (&ep)[V], uint32_t nxt,
+    uint32_t prv, bool stream, uint32_t x0, uint32_t nv, uint32_t r, uint32_t t, const PlainArgs &p,
+    const SliceTables &tab, uint32_t (&om)[V], uint32_t (&o0)[V], uint32_t (&op)[V], uint32_t &err,
+    InputsUsed &&inputs_used)
+{
+    // pre-collision occupations n_i(x) = B_i(x - v_i), for a full vector ...
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        om[j] = stream ? (j + 1 < V ? em[j + 1] : nxt) : em[j];
+        o0[j] = e0[j];
+        op[j] = stream ? (j > 0 ? ep[j - 1] : prv) : ep[j];
+    }
+    // ... and at the end of a replica: the last node wraps around, padding stays empty
+    if (nv < uint32_t(V)) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (stream && uint32_t(j) + 1u == nv) om[j] = nxt;
+            if (uint32_t(j) >= nv) om[j] = o0[j] = op[j] = 0u;
+        }
+    }
+    uint32_t heavy = 0, on = 0;  // bit j: node j beyond the tables / drawn from them
+    uint32_t rs[V];
+    const uint32_t stride = tab.n_max + 1u;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const uint32_t a = om[j], b = o0[j], c = op[j];
+        const uint32_t N = a + b + c, Jp = a > c ? a - c : c - a;
+        const bool drawn = N >= 2u && N <= tab.n_max;
+        heavy |= uint32_t(N > tab.n_max) << j;
+        on |= uint32_t(drawn) << j;
+        rs[j] = __ldg(tab.rowstart + (drawn ? N * stride + Jp : 0u));
+    }
+    inputs_used();
+    uint32_t lo[V], hi[V];
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) {
+        uint32_t w0 = (x0 >> 1) + uint32_t(i), w1 = r, w2 = t, w3 = kPurposeSlice << 28;
+        philox4x32_10(w0, w1, w2, w3, p.rk);
+        lo[2 * i] = w0;
+        hi[2 * i] = w1;
+        lo[2 * i + 1] = w2;
+        hi[2 * i + 1] = w3;
+    }
+    uint32_t e[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        // a state's row within its (N, |J|) slice is b / 2 (b has the parity of N - |J|)
+        rs[j] += o0[j] >> 1;
+        const uint32_t bucket = hi[j] >> (32 - kSliceBucketBits);
+        const bool drawn = (on >> j) & 1u;
+        e[j] = kNarrow
+            ? __ldg(tab.guide + (drawn ? rs[j] * uint32_t(kSliceBuckets) + bucket : 0u))
+            : __ldg(tab.guide + (drawn ? (uint64_t(rs[j]) << kSliceBucketBits) + bucket : 0ull));
+    }
+    uint32_t open = 0;  // bit j: the guide entry leaves node j's draw undecided
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const uint32_t inside = (e[j] >> 5) & 3u;  // entries in Q's bucket (3: three or more)
+        const uint32_t qn = (hi[j] >> (24 - kSliceBucketBits)) & 0xFFu, fn = e[j] >> 8;
+        const bool one = inside == 1u && qn != fn;  // the next 8 bits decide Q against it
+        open |= uint32_t(inside != 0u && !one) << j;
+        e[j] = (e[j] & 0x1Fu) + uint32_t(one && qn > fn);  // the count so far
+    }
+    open &= on;
+    if (open) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (!((open >> j) & 1u)) continue;
+            const uint32_t a = om[j], b = o0[j], c = op[j];
+            const uint32_t Jp = a > c ? a - c : c - a;
+            const uint32_t nvalid = min(p.C, (a + c - Jp) >> 1) + min(p.C, b >> 1);
+            e[j] = slice_finish(e[j], nvalid, (uint64_t(hi[j]) << 32) | lo[j],
+                                tab.secondary + uint64_t(rs[j]) * kSliceRowU64, err);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        // d = dmin + count with dmin = -min(C, b / 2): b' = b + 2 d and, with N and
+        // J kept, a' = a - d, c' = c - d (arithmetic modulo 2^32)
+        const uint32_t d = ((on >> j) & 1u) ? e[j] - min(p.C, o0[j] >> 1) : 0u;
+        om[j] -= d;
+        o0[j] += 2u * d;
+        op[j] -= d;
+    }
+    return heavy;
+}
+
+// Append the warp's heavy nodes (bit j of `heavy`: node node0 + j) to the list
+// of the sequential pass: one atomic per warp and node slot that has any.
+template <int V>
+__device__ __forceinline__ void list_heavy(uint32_t heavy, uint64_t node0, uint32_t lane,
+                                           const SliceTables &tab)
+{
+    if (!__any_sync(0xFFFFFFFFu, heavy != 0u)) return;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, (heavy >> j) & 1u);
+        if (!m) continue;
+        const uint32_t leader = __ffs(m) - 1u;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(tab.heavy_ctl, uint32_t(__popc(m)));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (m & (1u << lane)) {
+            const uint32_t i = base + __popc(m & ((1u << lane) - 1u));
+            if (i < tab.heavy_cap) tab.heavy_pos[i] = node0 + uint32_t(j);
+            else atomicOr(tab.heavy_ctl + 1, 1u);
+        }
+    }
+}
+
 // kMinBlocks counts CTAs of 256 threads (the register bound of the variant
-// table); the kernel runs CTAs of kSliceThreads.
-template <int V, int kMinBlocks, bool kOne, bool kNarrow>
+// table); the kernel runs CTAs of kSliceThreads.  kStream: pull-stream before
+// colliding (else collide only).  kOne: a single replica, whose node indices
+// fit 32 bits.
+template <int V, int kMinBlocks, bool kOne, bool kNarrow, bool kStream>
 __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThreads)
     k_step_slice(PlainArgs p, SliceTables tab)
 {
     static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
-    const bool kStream = p.stream != 0u;
     using T = typename VecT<V>::T;
+    using Index = typename std::conditional<kOne, uint32_t, uint64_t>::type;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t v_begin = p.g_begin * (8 / V), v_end = p.g_end * (8 / V);
-    const uint64_t g = v_begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const Index v_begin = Index(p.g_begin) * (8 / V), v_end = Index(p.g_end) * (8 / V);
+    const Index g = v_begin + Index(blockIdx.x) * blockDim.x + threadIdx.x;
     const bool active = g < v_end;
-    const uint64_t gv = active ? g : v_end - 1;  // idle lanes mirror the last vector
-    const uint64_t node0 = gv * V;
+    const Index gv = active ? g : v_end - 1;  // idle lanes mirror the last vector
+    const Index node0 = gv * V;
 
-    uint64_t off;
+    Index off;
     uint32_t L, rid;
     if (kOne) {
-        off = p.one_off;
+        off = Index(p.one_off);
         L = p.one_L;
         rid = p.one_rid;
     } else {
@@ -130,33 +313,10 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
     const uint32_t nv = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
     const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
 
-    uint32_t err = 0, heavy = 0;
+    uint32_t err = 0;
     uint32_t om[V], o0[V], op[V];
-#pragma unroll
-    for (int i = 0; i < V / 2; ++i) {
-        uint32_t w0 = (x0 >> 1) + uint32_t(i), w1 = rid + p.r0, w2 = t, w3 = kPurposeSlice << 28;
-        philox4x32_10(w0, w1, w2, w3, p.rk);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = 2 * i + h;
-            // pre-collision occupations n_i(x) = B_i(x - v_i); padding stays empty
-            uint32_t a, b, c;
-            if (kStream) {
-                a = (uint32_t(j) + 1u < nv) ? em[(j + 1) % V] : nxt;
-                c = (j > 0) ? ep[(j + V - 1) % V] : prv;
-            } else {
-                a = em[j];
-                c = ep[j];
-            }
-            b = e0[j];
-            if (uint32_t(j) >= nv) a = b = c = 0u;
-            if (slice_node<kNarrow>(a, b, c, h ? w2 : w0, h ? w3 : w1, tab, p.C, err))
-                heavy |= 1u << j;
-            om[j] = a;
-            o0[j] = b;
-            op[j] = c;
-        }
-    }
+    uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, x0, nv, rid + p.r0,
+                                              t, p, tab, om, o0, op, err);
     if (active) {
         T vo;
         pack(om, vo);
@@ -167,25 +327,228 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
         __stcs(reinterpret_cast<T *>(p.out + 2 * p.P + node0), vo);
         flag_error(p.err, err);
     }
-    // heavy nodes (written unchanged) join the list of the sequential pass:
-    // one atomic per warp and node slot that has any
+    // heavy nodes (written unchanged) join the list of the sequential pass
     if (!active) heavy = 0u;
-    if (__any_sync(0xFFFFFFFFu, heavy != 0u)) {
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, (heavy >> j) & 1u);
-            if (!m) continue;
-            const uint32_t leader = __ffs(m) - 1u;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(tab.heavy_ctl, uint32_t(__popc(m)));
-            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-            if (m & (1u << lane)) {
-                const uint32_t i = base + __popc(m & ((1u << lane) - 1u));
-                if (i < tab.heavy_cap) tab.heavy_pos[i] = node0 + uint32_t(j);
-                else atomicOr(tab.heavy_ctl + 1, 1u);
-            }
+    list_heavy<V>(heavy, uint64_t(node0), lane, tab);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised form for one replica (the single-lattice step).  A
+// producer warp streams tiles of T = W x 32 x 8 nodes of the three planes into
+// a ring of S shared-memory stages with bulk asynchronous copies
+// (cp.async.bulk, each stage's bytes counted on its "full" mbarrier); W
+// consumer warps read a stage into registers, hand it back through its
+// "empty" mbarrier at once, draw every node's C sub-collisions from the tables
+// and store the post-collision vectors straight to global memory.  The bytes
+// in flight live in shared memory instead of registers, so HBM streaming no
+// longer competes with the table lookups for warps.  Every wait is bounded:
+// after about two seconds it sets the timeout bit of the error word and the
+// CTA stops (the producer first lets the copies it issued land).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kWaitCycles = 4000000000ll;  // bounded mbarrier waits (~2 s at 2 GHz)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// Wait for the phase of `parity` to complete; false after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const long long start = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - start > kWaitCycles) return false;
+    return true;
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completion counted on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace
+
+// Shared memory of one stage: plane -1 holds nodes [x0, x0 + T + 8), plane 0
+// nodes [x0, x0 + T), plane +1 nodes [x0 - 8, x0 + T) (one 16-byte halo vector
+// on the side each plane streams from).
+template <int W, int V>
+struct WsTile {
+    static constexpr uint32_t T = uint32_t(W) * 32u * uint32_t(V);  // nodes per tile
+    static constexpr uint32_t kBuf = T + 8u;                // nodes per plane buffer
+    static constexpr uint32_t kStage = 3u * kBuf;           // uint16 per stage
+};
+
+template <int W, int V, int S, int kMinBlocks, bool kNarrow>
+__global__ void __launch_bounds__((W + 1) * 32, kMinBlocks)
+    k_step_slice_ws(PlainArgs p, SliceTables tab)
+{
+    static_assert(V == 4 || V == 8, "V nodes per consumer thread: 4 or 8");
+    using Tl = WsTile<W, V>;
+    using Vec = typename VecT<V>::T;
+    constexpr uint32_t T = Tl::T, kBuf = Tl::kBuf;
+    extern __shared__ __align__(128) uint16_t ring[];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint64_t off = p.one_off;
+    const uint32_t L = p.one_L;
+    const uint32_t Pn = (L + 7u) & ~7u;  // the replica's nodes with padding
+    const uint32_t tiles = (Pn + T - 1u) / T;
+    const uint16_t *__restrict__ inm = p.in + off;
+    const uint16_t *__restrict__ in0 = p.in + p.P + off;
+    const uint16_t *__restrict__ inp = p.in + 2 * p.P + off;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1u);
+            mbar_init(&empty[s], uint32_t(W));
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+
+    if (warp == uint32_t(W)) {
+        // producer: one lane issues the copies of this CTA's tiles in order
+        if (lane != 0u) return;
+        uint32_t i = 0, issued = 0;
+        bool ok = true;
+        for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
+            const uint32_t s = i % S, round = i / S;
+            if (round > 0u && !mbar_wait(&empty[s], (round - 1u) & 1u)) {
+                ok = false;
+                break;
+            }
+            const uint32_t x0 = tile * T, n = min(T, Pn - x0);
+            const uint32_t nm = min(n + 8u, Pn - x0);             // plane -1: one vector beyond
+            const uint32_t lo = x0 >= 8u ? 8u : 0u;               // plane +1: one vector before
+            uint16_t *st = ring + size_t(s) * Tl::kStage;
+            mbar_expect_tx(&full[s], 2u * (nm + n + n + lo));
+            bulk_load(st, inm + x0, 2u * nm, &full[s]);
+            bulk_load(st + kBuf, in0 + x0, 2u * n, &full[s]);
+            bulk_load(st + 2u * kBuf + (8u - lo), inp + x0 - lo, 2u * (n + lo), &full[s]);
+            ++issued;
+        }
+        if (!ok) {
+            flag_error(p.err, kErrTimeout);
+            // let the copies already issued land before the CTA's memory goes away
+            for (uint32_t k = issued > uint32_t(S) ? issued - S : 0u; k < issued; ++k)
+                mbar_wait(&full[k % S], (k / S) & 1u);
+        }
+        return;
+    }
+
+    // consumers
+    const bool kStream = p.stream != 0u;
+    const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
+    const uint32_t r = p.one_rid + p.r0;
+    const uint32_t xl = (warp * 32u + lane) * uint32_t(V);  // tile-local first node of this thread
+    uint32_t err = 0, i = 0;
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
+        const uint32_t s = i % S, round = i / S;
+        if (!mbar_wait(&full[s], round & 1u)) {
+            err |= kErrTimeout;
+            break;
+        }
+        const uint32_t x0t = tile * T, n = min(T, Pn - x0t);
+        const uint32_t x0 = x0t + xl;  // replica-local first node of this thread
+        const uint16_t *st = ring + size_t(s) * Tl::kStage;
+        const uint16_t *sm = st, *sz = st + kBuf, *sp = st + 2u * kBuf + 8u;  // index x - x0t
+        uint32_t em[V], e0[V], ep[V];
+        unpack(*reinterpret_cast<const Vec *>(sm + xl), em);
+        unpack(*reinterpret_cast<const Vec *>(sz + xl), e0);
+        unpack(*reinterpret_cast<const Vec *>(sp + xl), ep);
+        // halo: B_-1(x0 + V) and B_+1(x0 - 1), from the neighbouring lanes, the
+        // stage's halo vectors, or (at the ends of the lattice) the periodic image
+        const bool own_next = !(lane < 31u && x0 + V < L), own_prev = !(lane > 0u && x0 > 0u);
+        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
+        uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
+        if (kStream && own_next) nxt = x0 + V < L ? uint32_t(sm[xl + V]) : uint32_t(inm[0]);
+        if (kStream && own_prev) prv = x0 > 0u ? uint32_t(sp[int(xl) - 1]) : uint32_t(inp[L - 1u]);
+
+        const bool active = xl < n;
+        const uint32_t nv = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
+        uint32_t om[V], o0[V], op[V];
+        // the stage goes back to the producer once every lane's reads of it have
+        // been consumed (arriving right after issuing the shared-memory loads let
+        // the next bulk copy overwrite values still in flight)
+        uint32_t heavy = slice_vector_phased<V, kNarrow>(
+            em, e0, ep, nxt, prv, kStream, x0, nv, r, t, p, tab, om, o0, op, err, [&]() {
+                __syncwarp();
+                if (lane == 0u) mbar_arrive(&empty[s]);
+            });
+        const uint64_t node0 = off + x0;
+        if (active) {
+            Vec vo;
+            pack(om, vo);
+            __stcs(reinterpret_cast<Vec *>(p.out + node0), vo);
+            pack(o0, vo);
+            __stcs(reinterpret_cast<Vec *>(p.out + p.P + node0), vo);
+            pack(op, vo);
+            __stcs(reinterpret_cast<Vec *>(p.out + 2 * p.P + node0), vo);
+        }
+        if (!active) heavy = 0u;
+        list_heavy<V>(heavy, node0, lane, tab);
+    }
+    flag_error(p.err, err);
+}
+
+template <int W, int V, int S, int kMinBlocks>
+static cudaError_t launch_slice_ws_v(const PlainArgs &p, const SliceTables &tab, cudaStream_t s)
+{
+    using Tl = WsTile<W, V>;
+    const size_t smem = size_t(S) * Tl::kStage * sizeof(uint16_t);
+    auto kern = tab.guide_narrow ? k_step_slice_ws<W, V, S, kMinBlocks, true>
+                                 : k_step_slice_ws<W, V, S, kMinBlocks, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (W + 1) * 32, smem)) !=
+        cudaSuccess)
+        return e;
+    const uint32_t Pn = (p.one_L + 7u) & ~7u;
+    const uint32_t tiles = (Pn + Tl::T - 1u) / Tl::T;
+    const uint32_t grid = std::min<uint32_t>(tiles, uint32_t(sms * std::max(per_sm, 1)));
+    kern<<<grid, (W + 1) * 32, smem, s>>>(p, tab);
+    return cudaGetLastError();
 }
 
 // The sequential pass over the step's heavy nodes (see above).  Reads the
@@ -246,18 +609,28 @@ static void launch_slice_v(const PlainArgs &p, bool one, const SliceTables &tab,
 {
     const uint64_t threads = (p.g_end - p.g_begin) * (8u / V);
     const dim3 grid(uint32_t((threads + kSliceThreads - 1) / kSliceThreads));
-    if (tab.guide_narrow) {
-        if (one) k_step_slice<V, kMinBlocks, true, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
-        else k_step_slice<V, kMinBlocks, false, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
-    } else {
-        if (one) k_step_slice<V, kMinBlocks, true, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
-        else k_step_slice<V, kMinBlocks, false, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
-    }
+    const bool narrow = tab.guide_narrow != 0u, stream = p.stream != 0u;
+#define MCLG_SLICE_LAUNCH(ONE, NARROW, STREAM)                                                  \
+    if (one == ONE && narrow == NARROW && stream == STREAM)                                     \
+        k_step_slice<V, kMinBlocks, ONE, NARROW, STREAM><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    MCLG_SLICE_LAUNCH(true, true, true)
+    MCLG_SLICE_LAUNCH(true, true, false)
+    MCLG_SLICE_LAUNCH(true, false, true)
+    MCLG_SLICE_LAUNCH(true, false, false)
+    MCLG_SLICE_LAUNCH(false, true, true)
+    MCLG_SLICE_LAUNCH(false, true, false)
+    MCLG_SLICE_LAUNCH(false, false, true)
+    MCLG_SLICE_LAUNCH(false, false, false)
+#undef MCLG_SLICE_LAUNCH
 }
 
-// Slice-kernel variants: (nodes per thread, minimum CTAs of 256 threads per
-// SM, i.e. a register bound).  The autotuner picks one per handle.
-static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8};
+// Slice-kernel variants 0-5: k_step_slice with (nodes per thread, minimum
+// CTAs of 256 threads per SM, i.e. a register bound); variants 6-9: the
+// warp-specialised k_step_slice_ws with (consumer warps, stages, minimum CTAs
+// per SM), 8 nodes per thread, for single-replica launches (a launch over
+// several replicas takes variant 4 instead).  The autotuner picks one per
+// handle; every variant gives the same bits.
+static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8, 8, 8, 8, 8};
 
 uint32_t slice_variant_vec(uint32_t variant)
 {
@@ -268,15 +641,23 @@ cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, c
 {
     if (p.g_end == p.g_begin) return cudaSuccess;
     if (p.variant >= kSliceVariants) return cudaErrorInvalidValue;
-    switch (p.variant) {
+    const uint32_t v = (!one && p.variant >= kSliceClassicVariants) ? 4u : p.variant;
+    cudaError_t e = cudaSuccess;
+    switch (v) {
     case 0: launch_slice_v<2, 8>(p, one, tab, s); break;  // <= 32 registers
     case 1: launch_slice_v<2, 6>(p, one, tab, s); break;  // <= 40 registers
     case 2: launch_slice_v<4, 5>(p, one, tab, s); break;  // <= 48 registers
     case 3: launch_slice_v<4, 4>(p, one, tab, s); break;  // <= 64 registers
     case 4: launch_slice_v<8, 3>(p, one, tab, s); break;  // <= 80 registers
-    default: launch_slice_v<8, 2>(p, one, tab, s); break; // <= 128 registers
+    case 5: launch_slice_v<8, 2>(p, one, tab, s); break;  // <= 128 registers
+    // (consumer warps, nodes per consumer thread, stages, CTAs per SM)
+    case 6: e = launch_slice_ws_v<16, 4, 6, 2>(p, tab, s); break;  // <= 60 registers
+    case 7: e = launch_slice_ws_v<4, 4, 8, 6>(p, tab, s); break;   // <= 68
+    case 8: e = launch_slice_ws_v<8, 4, 6, 4>(p, tab, s); break;   // <= 56
+    default: e = launch_slice_ws_v<2, 4, 12, 10>(p, tab, s); break; // <= 68
     }
-    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (one) k_step_heavy<true><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
     else k_step_heavy<false><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);

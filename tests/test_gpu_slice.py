@@ -108,10 +108,11 @@ def test_slice_full_size_sampled_nodes():
         assert after[2, (y + 1) % L] == nc      # v = +1 moved right
 
 
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(10))
 def test_slice_every_launch_variant_bit_exact(variant):
     """Each launch shape of the slice kernel (2, 4 or 8 nodes per thread, register
-    bounds) gives the oracle's bits, on ragged replicas whose ends fall inside a
+    bounds; the warp-specialised form with bulk-copy stages for single-replica
+    launches) gives the oracle's bits, on ragged replicas whose ends fall inside a
     thread's vector, on one long lattice, and without streaming."""
     L = [8, 3, 100, 1, 517, 64, 6]
     n0 = workloads.random_state(L, 40.0, seed=variant)
@@ -125,7 +126,12 @@ def test_slice_every_launch_variant_bit_exact(variant):
     assert err == 0
     assert np.array_equal(run_slice([4099], 6, n1, 1, 3, kernel_variant=variant), want)
     with pytest.raises(mclg.MCLGError):
-        mclg.Lattice(L, sampler=SLICE, kernel_variant=6)  # six variants: 0 .. 5
+        mclg.Lattice(L, sampler=SLICE, kernel_variant=10)  # ten variants: 0 .. 9
+    for Ls in ([1], [7], [8], [1031], [3 * 4096 + 13]):     # tails inside a tile and a vector
+        n2 = workloads.random_state(Ls, 45.0, seed=Ls[0])
+        want, err = oracle.slice_step(Ls, 6, n2, 9, 5)
+        assert err == 0
+        assert np.array_equal(run_slice(Ls, 6, n2, 9, 5, kernel_variant=variant), want), Ls
     want, err = oracle.slice_step(L, 5, n0, 2, 4, flags=oracle.FLAG_NO_STREAM)
     assert err == 0
     got = run_slice(L, 5, n0, 2, 4, flags=mclg.NO_STREAM, kernel_variant=variant)
@@ -145,3 +151,17 @@ def test_slice_galilean_rate_bit_exact():
         assert err == 0
         got = run_slice(L, 21, n0, 3, 12, lam=(3, 4), flags=mclg.GALILEAN, slice_n_max=n_max)
         assert np.array_equal(got, want), n_max
+
+
+@pytest.mark.parametrize("variant", [6, 7, 8, 9])
+def test_warp_specialised_ring_wraps_many_times(variant):
+    """A lattice long enough that every CTA of the warp-specialised kernel cycles
+    through its ring of shared-memory stages several times (2^24 + 12345 nodes,
+    a tail inside the last tile and inside a vector), two steps, every node."""
+    L = [(1 << 24) + 12345]
+    n0 = workloads.random_state(L, 33.0, seed=variant)
+    want, err = oracle.slice_step(L, 17, n0, 40, 2)
+    assert err == 0
+    got = run_slice(L, 17, n0, 40, 2, kernel_variant=variant)
+    bad = np.nonzero((got != want).any(axis=0))[0]
+    assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
