@@ -76,6 +76,12 @@ typedef enum {
                              collides with lambda(N, J) = q / 256, q the largest integer with
                              q / 256 <= lambda / sqrt(1 + 3 u^2), u = J / N, lambda the
                              handle's lambda_num / lambda_den; both samplers */
+#define MCLG_HALO 8u      /* the handle's one replica is a block of a larger periodic lattice
+                             (domain decomposition over ranks): its node x is the lattice's
+                             node node_offset + x for every random number, and its two edges
+                             exchange one value each per step with the neighbouring blocks
+                             (mclg_halo_get / mclg_halo_put).  One replica, no MCLG_STATS, not
+                             MCLG_MODE_PERSISTENT; with the SLICE sampler node_offset is even. */
 
 /* samplers: two exact ways to draw the C sub-collisions of a node, with
  * different uses of the random bits (each is bit-exact to its own oracle):
@@ -128,10 +134,13 @@ typedef struct {
                                 applies to single-replica launches; reported by mclg_tuning).
                                 Every variant gives the same bits; this only fixes the launch
                                 shape. */
+    uint32_t node_offset;    /* MCLG_HALO: index of the block's first node in the whole lattice
+                                (node_offset + L[0] <= 2^32); must be 0 without MCLG_HALO */
 } mclg_params;
 
 /* Defaults: C = 10, lambda = 1, flags 0, mode AUTO, first_replica 0,
- * SEQUENTIAL sampler (the paper's D1Q3 runs), slice_n_max 0, kernel_variant 0. */
+ * SEQUENTIAL sampler (the paper's D1Q3 runs), slice_n_max 0, kernel_variant 0,
+ * node_offset 0. */
 void mclg_default_params(mclg_params *p);
 
 /* Create a handle for `replicas` independent periodic lattices of lengths
@@ -193,6 +202,33 @@ uint64_t mclg_time(mclg_handle h);
  * units, cfg[4] = persistent register-bound variant (0, 1, 2 = 1, 2, 3 CTAs of
  * 512 threads per SM), cfg[5] = 0 (reserved). */
 mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6]);
+
+/* Domain decomposition of one periodic lattice (MCLG_HALO handles).  The
+ * evolution equation (Sec. III) moves one population per link and step, so
+ * across each cut one value leaves and one arrives per step.  A rank owning
+ * global nodes [node_offset, node_offset + L) steps with
+ *     mclg_step(h, 1); mclg_halo_get(h, out);
+ *     send out[0] to the left neighbour and out[1] to the right neighbour,
+ *     receive in[0] from the left neighbour (its out[1]) and in[1] from the
+ *     right neighbour (its out[0]);
+ *     mclg_halo_put(h, in);
+ * and the blocks together reproduce the undecomposed lattice bit for bit (the
+ * random numbers are keyed by the global node index).  One block whose out is
+ * put back crossed over, in = (out[1], out[0]), is the periodic lattice.
+ *
+ * mclg_halo_get: out[0] = the post-collision v = -1 occupation of the block's
+ * first node, out[1] = the post-collision v = +1 occupation of its last node,
+ * from the last mclg_step (2 uint16, host or device; a host destination
+ * synchronises).  MCLG_ERR_STATE before the first step.
+ * mclg_halo_put: the arriving values in[0] (v = +1, into the first node) and
+ * in[1] (v = -1, into the last node) complete the field n(x, t); required
+ * after every mclg_step before the next mclg_step, mclg_get_state or
+ * mclg_moments (MCLG_ERR_STATE otherwise).  mclg_init and mclg_set_state
+ * take the edge values from the given field.  mclg_step advances one step per
+ * call on such a handle (n_steps > 1 returns MCLG_ERR_ARG).  Both calls are
+ * asynchronous for device pointers (ordered on the handle's stream). */
+mclg_status mclg_halo_get(mclg_handle h, uint16_t *out);
+mclg_status mclg_halo_put(mclg_handle h, const uint16_t *in);
 
 /* Release every resource of the handle.  NULL-safe. */
 void mclg_destroy(mclg_handle h);

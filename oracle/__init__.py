@@ -79,6 +79,11 @@ def _load():
             lib.orc_stats_accumulate.argtypes = [u32, u32, P, P, P, P, P]
             lib.orc_exact_cov.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, u64]
             lib.orc_exact_cov.restype = ctypes.c_double
+            lib.orc_block_collide.argtypes = [u32, u32, u32, u64, u32, u32, u32, u32, u32, u32,
+                                              P, P, u32, P]
+            lib.orc_block_collide.restype = i32
+            lib.orc_block_stream.argtypes = [u32, P, P, P]
+            lib.orc_block_stream.restype = None
             lib.orc_set_threads.argtypes = [i32]
             lib.orc_set_threads.restype = i32
             lib.orc_threads.argtypes = []
@@ -254,3 +259,30 @@ class Stats:
         p = pairs.index((min(i, j), max(i, j)))
         return float(_load().orc_exact_cov(int(self.s2[x, p]), int(self.s1[x, i]),
                                            int(self.s1[x, j]), self.count))
+
+
+class Block:
+    """One block of a periodic lattice, global nodes [x0, x0 + len(n)), for a
+    decomposition over ranks: collide() returns the two values that leave the
+    block, stream(in) takes the two that arrive (see orc_block_collide)."""
+
+    def __init__(self, n, x0: int, seed: int, C: int = 10, lam=(1, 1), flags: int = 0,
+                 replica: int = 0, sampler: str = "sequential", n_max: int = SLICE_N_MAX):
+        self.n = np.ascontiguousarray(np.asarray(n, dtype=np.uint16).reshape(3, -1)).copy()
+        self.Lb = int(self.n.shape[1])
+        self.x0, self.seed, self.C, self.lam, self.flags = int(x0), int(seed), int(C), lam, flags
+        self.replica = int(replica)
+        self.sampler = 1 if sampler == "slice" else 0
+        self.n_max = int(n_max)
+        self.post = np.zeros_like(self.n)
+
+    def collide(self, t: int) -> tuple[np.ndarray, int]:
+        out = np.zeros(2, dtype=np.uint16)
+        err = _load().orc_block_collide(self.Lb, self.x0, self.replica, self.seed & (2**64 - 1),
+                                        self.C, self.lam[0], self.lam[1], self.flags, self.sampler,
+                                        self.n_max, _ptr(self.n), _ptr(self.post), t, _ptr(out))
+        return out, int(err)
+
+    def stream(self, incoming) -> None:
+        inc = np.ascontiguousarray(np.asarray(incoming, dtype=np.uint16).reshape(2))
+        _load().orc_block_stream(self.Lb, _ptr(self.post), _ptr(inc), _ptr(self.n))

@@ -930,3 +930,76 @@ int orc_slice_step(const uint32_t *L, uint32_t R, uint64_t seed, uint32_t C, uin
     free(post);
     return err;
 }
+
+/* ------------------------------------------------------------------------ */
+/* One block of a larger periodic lattice (domain decomposition of a single  */
+/* lattice over several ranks).  The evolution equation of Sec. III moves    */
+/* one particle population per link and step: across the cut on each side of */
+/* a block, one value leaves and one arrives per step.                       */
+/*                                                                          */
+/* The block holds global nodes [x0, x0 + Lb) of a lattice whose random      */
+/* numbers are keyed by the global node index (replica index r).  A step is  */
+/* split in two at the exchange:                                             */
+/*   orc_block_collide  the C sub-collisions of every node of the block at    */
+/*                      time t (sampler 0 sequential, 1 slice with n_max),   */
+/*                      giving the post-collision field; out[0] = the v = -1 */
+/*                      value of the first node (it leaves to the left),     */
+/*                      out[1] = the v = +1 value of the last node (it       */
+/*                      leaves to the right);                                */
+/*   orc_block_stream   streaming inside the block; the first node's v = +1  */
+/*                      value is in[0] (from the left neighbour's out[1]),   */
+/*                      the last node's v = -1 value is in[1] (from the      */
+/*                      right neighbour's out[0]).                           */
+/* With one block covering the lattice and in = (out[1], out[0]) this is     */
+/* exactly orc_step / orc_slice_step.                                        */
+/* ------------------------------------------------------------------------ */
+int orc_block_collide(uint32_t Lb, uint32_t x0, uint32_t r, uint64_t seed, uint32_t C,
+                      uint32_t lam_n, uint32_t lam_d, uint32_t flags, uint32_t sampler,
+                      uint32_t n_max, const uint16_t *n, uint16_t *post, uint32_t t,
+                      uint16_t out[2])
+{
+    if (sampler == 1 && C > SLICE_MAX_C) return 8;
+    uint32_t key[2];
+    seed_key(seed, key);
+    int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+    for (uint32_t y = 0; y < Lb; y++) {
+        uint32_t x = x0 + y; /* global node index: the random numbers' counter */
+        uint32_t a = n[y], b = n[Lb + y], c = n[2 * (uint64_t)Lb + y];
+        uint32_t N = a + b + c;
+        int32_t J = (int32_t)c - (int32_t)a;
+        uint32_t ln, ld;
+        node_lambda(flags, N, J, lam_n, lam_d, &ln, &ld);
+        if (sampler == 0 || N > n_max) {
+            uint16_t st[3] = {(uint16_t)a, (uint16_t)b, (uint16_t)c};
+            err |= collide_node(st, x, r, t, C, ln, ld, key);
+            a = st[0];
+            b = st[1];
+            c = st[2];
+        } else if (N >= 2) {
+            int64_t nb = orc_slice_draw(N, J, b, orc_slice_q(x, r, t, key), C, ln, ld);
+            if (nb < 0) {
+                err |= ORC_ERR_SAMPLER;
+            } else {
+                b = (uint32_t)nb;
+                a = (uint32_t)(((int64_t)N - J - nb) / 2);
+                c = (uint32_t)(((int64_t)N + J - nb) / 2);
+            }
+        }
+        post[y] = (uint16_t)a;
+        post[Lb + y] = (uint16_t)b;
+        post[2 * (uint64_t)Lb + y] = (uint16_t)c;
+    }
+    out[0] = post[0];
+    out[1] = post[2 * (uint64_t)Lb + Lb - 1];
+    return err;
+}
+
+void orc_block_stream(uint32_t Lb, const uint16_t *post, const uint16_t in[2], uint16_t *n)
+{
+    for (uint32_t y = 0; y < Lb; y++) {
+        n[y] = y + 1 < Lb ? post[y + 1] : in[1];                          /* v = -1 from the right */
+        n[Lb + y] = post[Lb + y];                                         /* v = 0 stays */
+        n[2 * (uint64_t)Lb + y] = y > 0 ? post[2 * (uint64_t)Lb + y - 1] : in[0]; /* v = +1 from the left */
+    }
+}

@@ -70,6 +70,11 @@ struct mclg_ctx {
     uint16_t *d_slice_guide = nullptr;
     unsigned long long *d_slice_secondary = nullptr;
     uint64_t stats_count = 0;
+    // a block of a larger lattice (MCLG_HALO): the two arriving edge values
+    bool halo = false;
+    bool halo_ready = false;          // the arriving values of the current time are in d_halo
+    bool stepped = false;             // a step has run since the state was set
+    uint16_t *d_halo = nullptr;       // [2]: v = +1 into node 0, v = -1 into node L - 1
 };
 
 namespace {
@@ -163,6 +168,8 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
     a.galilean = (h->prm.flags & MCLG_GALILEAN) ? 1u : 0u;
     a.r0 = h->prm.first_replica;
     a.t_dev = nullptr;
+    a.halo_in = h->halo ? h->d_halo : nullptr;
+    a.x_base = h->prm.node_offset;
     a.rk = make_round_keys(h->seed);
     return a;
 }
@@ -490,6 +497,7 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
 
 uint32_t effective_mode(const mclg_ctx *h)
 {
+    if (h->halo) return MCLG_MODE_PLAIN;       // one block, edges exchanged every step
     if (h->prm.flags & MCLG_STATS) return 3u;  // batched plain: state in HBM after each step
     if (h->prm.sampler == MCLG_SAMPLER_SLICE)  // the slice kernel has no persistent form
         return (h->prm.mode == MCLG_MODE_PLAIN || h->R == 1) ? MCLG_MODE_PLAIN : 3u;
@@ -546,7 +554,7 @@ int init_range(const mclg_ctx *h, const double *rho, const double *u, uint16_t *
             const double part_mu = mu / double(parts);
             uint64_t total = 0;
             for (uint32_t q = 0; q < parts; ++q) {
-                uint32_t w0 = x, w1 = r + h->prm.first_replica, w2 = q / 2,
+                uint32_t w0 = h->prm.node_offset + x, w1 = r + h->prm.first_replica, w2 = q / 2,
                          w3 = (kPurposeInit << 28) | i;
                 philox4x32_10(w0, w1, w2, w3, k0, k1);
                 const uint32_t lo = (q & 1u) ? w2 : w0, hi = (q & 1u) ? w3 : w1;
@@ -575,6 +583,16 @@ mclg_status upload_state(mclg_ctx *h, const uint16_t *n, uint64_t t)
     }
     MCLG_CK(launch_to_device_form(src, h->S, h->d_B[h->cur], h->lay, streaming(h) ? 1 : 0,
                                   h->stream));
+    if (h->halo) {
+        // the edge values that arrived from the neighbouring blocks are part of the
+        // given field: v = +1 at node 0 and v = -1 at node L - 1
+        MCLG_CK(cudaMemcpyAsync(h->d_halo, src + 2 * h->S, sizeof(uint16_t),
+                                cudaMemcpyDeviceToDevice, h->stream));
+        MCLG_CK(cudaMemcpyAsync(h->d_halo + 1, src + (h->S - 1), sizeof(uint16_t),
+                                cudaMemcpyDeviceToDevice, h->stream));
+        h->halo_ready = true;
+        h->stepped = false;
+    }
     MCLG_CK(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
     if (!dev) MCLG_CK(cudaStreamSynchronize(h->stream));  // the caller may free n on return
     h->t = t;
@@ -599,6 +617,7 @@ void mclg_default_params(mclg_params *p)
     p->sampler = MCLG_SAMPLER_SEQUENTIAL;
     p->slice_n_max = 0;
     p->kernel_variant = 0;
+    p->node_offset = 0;
 }
 
 const char *mclg_status_str(mclg_status s)
@@ -653,6 +672,7 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->st.m2c);
     cudaFree(h->st.count);
     cudaFree(h->d_stat_partials);
+    cudaFree(h->d_halo);
     delete h;
 }
 
@@ -666,7 +686,19 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     mclg_default_params(&prm);
     if (p) prm = *p;
     if (prm.lambda_den < 1 || prm.lambda_den > 256 || prm.lambda_num > prm.lambda_den) return MCLG_ERR_ARG;
-    if (prm.mode > MCLG_MODE_BATCHED || (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS | MCLG_GALILEAN))) return MCLG_ERR_ARG;
+    if (prm.mode > MCLG_MODE_BATCHED ||
+        (prm.flags & ~(MCLG_NO_STREAM | MCLG_STATS | MCLG_GALILEAN | MCLG_HALO)))
+        return MCLG_ERR_ARG;
+    if (prm.flags & MCLG_HALO) {
+        // one block of a larger periodic lattice: one replica, global node indices < 2^32,
+        // node pairs of the slice sampler's random numbers aligned with the lattice's
+        if (replicas != 1 || (prm.flags & MCLG_STATS) || prm.mode == MCLG_MODE_PERSISTENT ||
+            uint64_t(prm.node_offset) + L[0] > (uint64_t(1) << 32) ||
+            (prm.sampler == MCLG_SAMPLER_SLICE && (prm.node_offset & 1u)))
+            return MCLG_ERR_ARG;
+    } else if (prm.node_offset != 0) {
+        return MCLG_ERR_ARG;
+    }
     uint64_t S = 0;
     for (uint32_t r = 0; r < replicas; ++r) {
         if (L[r] == 0 || L[r] > (uint32_t(1) << 31)) return MCLG_ERR_ARG;
@@ -763,6 +795,8 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         !alloc((void **)&h->lay.d_rep_id, replicas * sizeof(uint32_t)) ||
         !alloc((void **)&h->lay.d_chunk_rep, chunk_rep.size() * sizeof(uint32_t)))
         return fail(MCLG_ERR_NOMEM);
+    h->halo = (prm.flags & MCLG_HALO) != 0;
+    if (h->halo && !alloc((void **)&h->d_halo, 2 * sizeof(uint16_t))) return fail(MCLG_ERR_NOMEM);
     if (cudaMemcpy(h->lay.d_abi_off, h->abi_off.data(), replicas * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->lay.d_rep_off, h->rep_off.data(), replicas * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->lay.d_rep_L, h->rep_L.data(), replicas * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -842,11 +876,12 @@ mclg_status mclg_init(mclg_handle h, const double *rho, const double *u)
 mclg_status mclg_get_state(mclg_handle h, uint16_t *n, uint64_t *t)
 {
     if (!h || !n) return MCLG_ERR_ARG;
-    if (!h->has_state) return MCLG_ERR_STATE;
+    if (!h->has_state || (h->halo && !h->halo_ready)) return MCLG_ERR_STATE;
     MCLG_CK(cudaSetDevice(h->device));
     const bool dev = is_device_ptr(n);
     uint16_t *dst = dev ? n : h->d_stage;
-    MCLG_CK(launch_from_device_form(h->d_B[h->cur], dst, h->S, h->lay, streaming(h) ? 1 : 0, h->stream));
+    MCLG_CK(launch_from_device_form(h->d_B[h->cur], dst, h->S, h->lay, streaming(h) ? 1 : 0,
+                                    h->halo ? h->d_halo : nullptr, h->stream));
     if (!dev)
         MCLG_CK(cudaMemcpyAsync(n, h->d_stage, 3 * h->S * sizeof(uint16_t), cudaMemcpyDeviceToHost,
                                 h->stream));
@@ -861,6 +896,11 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
     if (h->t + n_steps > kMaxT) return MCLG_ERR_ARG;
     if (h->sticky) return status_from_bits(h->sticky);
     if (n_steps == 0) return MCLG_OK;
+    if (h->halo) {
+        // a block exchanges its edge values after every step
+        if (n_steps != 1) return MCLG_ERR_ARG;
+        if (!h->halo_ready) return MCLG_ERR_STATE;
+    }
     MCLG_CK(cudaSetDevice(h->device));
     const uint32_t mode = effective_mode(h);
     if (h->prm.sampler == MCLG_SAMPLER_SLICE) {
@@ -879,6 +919,10 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
             if (st != MCLG_OK) return st;
             h->cur = c;
             h->t += n_steps;
+            if (h->halo) {
+                h->halo_ready = false;  // the neighbours' values for the new time are still to come
+                h->stepped = true;
+            }
             if (h->prm.flags & MCLG_STATS) h->stats_count += n_steps * h->R;
         } else {
             // the per-replica baseline: one launch per replica and step
@@ -943,7 +987,7 @@ mclg_status mclg_step(mclg_handle h, uint64_t n_steps)
 mclg_status mclg_moments(mclg_handle h, int32_t *N, int32_t *J, int64_t *totals)
 {
     if (!h) return MCLG_ERR_ARG;
-    if (!h->has_state) return MCLG_ERR_STATE;
+    if (!h->has_state || (h->halo && !h->halo_ready)) return MCLG_ERR_STATE;
     MCLG_CK(cudaSetDevice(h->device));
     const bool devN = N && is_device_ptr(N), devJ = J && is_device_ptr(J);
     if ((N && !devN) || (J && !devJ)) {
@@ -955,7 +999,8 @@ mclg_status mclg_moments(mclg_handle h, int32_t *N, int32_t *J, int64_t *totals)
     int32_t *dN = N ? (devN ? N : h->d_stageNJ) : nullptr;
     int32_t *dJ = J ? (devJ ? J : h->d_stageNJ + h->S) : nullptr;
     MCLG_CK(cudaMemsetAsync(h->d_totals, 0, 2 * sizeof(unsigned long long), h->stream));
-    MCLG_CK(launch_moments(h->d_B[h->cur], dN, dJ, h->lay, streaming(h) ? 1 : 0, h->d_totals, h->stream));
+    MCLG_CK(launch_moments(h->d_B[h->cur], dN, dJ, h->lay, streaming(h) ? 1 : 0,
+                           h->halo ? h->d_halo : nullptr, h->d_totals, h->stream));
     if (N && !devN)
         MCLG_CK(cudaMemcpyAsync(N, dN, h->S * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     if (J && !devJ)
@@ -1035,6 +1080,36 @@ mclg_status mclg_sync(mclg_handle h)
 }
 
 uint64_t mclg_time(mclg_handle h) { return h ? h->t : 0; }
+
+mclg_status mclg_halo_get(mclg_handle h, uint16_t *out)
+{
+    if (!h || !out || !h->halo) return MCLG_ERR_ARG;
+    if (!h->stepped) return MCLG_ERR_STATE;
+    MCLG_CK(cudaSetDevice(h->device));
+    // post-collision values of the last step, kept where they were collided
+    // (the device form): v = -1 of node 0 and v = +1 of node L - 1
+    const uint16_t *B = h->d_B[h->cur];
+    const bool dev = is_device_ptr(out);
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    MCLG_CK(cudaMemcpyAsync(out, B + h->rep_off[0], sizeof(uint16_t), kind, h->stream));
+    MCLG_CK(cudaMemcpyAsync(out + 1, B + 2 * h->lay.P + h->rep_off[0] + h->L[0] - 1,
+                            sizeof(uint16_t), kind, h->stream));
+    if (!dev) return collect_errors(h);
+    return MCLG_OK;
+}
+
+mclg_status mclg_halo_put(mclg_handle h, const uint16_t *in)
+{
+    if (!h || !in || !h->halo) return MCLG_ERR_ARG;
+    if (!h->stepped) return MCLG_ERR_STATE;
+    MCLG_CK(cudaSetDevice(h->device));
+    const bool dev = is_device_ptr(in);
+    MCLG_CK(cudaMemcpyAsync(h->d_halo, in, 2 * sizeof(uint16_t),
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (!dev) MCLG_CK(cudaStreamSynchronize(h->stream));  // the caller may reuse `in` on return
+    h->halo_ready = true;
+    return MCLG_OK;
+}
 
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,

@@ -54,6 +54,11 @@ struct PlainArgs {
     uint32_t galilean; // 1: per-node rate lambda / sqrt(1 + 3 u^2) (galilean_q)
     uint32_t r0;       // random-stream index of replica id 0
     const uint32_t *t_dev;  // if set, the time step is *t_dev + t (graph replays)
+    // a block of a larger lattice (single-replica launches only): halo_in[0] is the
+    // v = +1 value entering node 0 from the left, halo_in[1] the v = -1 value entering
+    // node L - 1 from the right; nullptr for a periodic replica
+    const uint16_t *halo_in;
+    uint32_t x_base;   // global index of node 0 in the random numbers' counters
     RoundKeys rk;      // Philox round keys of the seed
 };
 
@@ -124,10 +129,12 @@ cudaError_t launch_persistent(const PersistentArgs &p, uint32_t n_units, uint32_
                               cudaStream_t s);
 cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, const Layout &lay,
                                   int stream, cudaStream_t s);
+// halo (or nullptr): for a block of a larger lattice, the two arriving values
+// that complete the canonical field (see PlainArgs::halo_in)
 cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,
-                                    int stream, cudaStream_t s);
+                                    int stream, const uint16_t *halo, cudaStream_t s);
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
-                           unsigned long long *totals, cudaStream_t s);
+                           const uint16_t *halo, unsigned long long *totals, cudaStream_t s);
 size_t stats_partials_bytes(uint32_t L, uint32_t R);
 // Statistics: the partial pass adds one step's exact sums to the batch sums;
 // the merge pass folds a batch of n samples per position (steps x R) into the

@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
     // take them from the neighbouring lanes.
     const bool own_next = !(lane < 31u && x0 + V < L), own_prev = !(lane > 0u && x0 > 0u);
     uint32_t nxt_own = 0u, prv_own = 0u;
-    if (kStream && own_next) nxt_own = inm[off + (x0 + V < L ? x0 + V : 0u)];
-    if (kStream && own_prev) prv_own = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
+    if (kStream && own_next)
+        nxt_own = x0 + V < L ? inm[off + x0 + V] : (kOne && p.halo_in ? p.halo_in[1] : inm[off]);
+    if (kStream && own_prev)
+        prv_own = x0 > 0u ? inp[off + x0 - 1u] : (kOne && p.halo_in ? p.halo_in[0] : inp[off + L - 1u]);
     uint32_t em[V], e0[V], ep[V];
     unpack(__ldcs(reinterpret_cast<const T *>(inm + node0)), em);
     unpack(__ldcs(reinterpret_cast<const T *>(in0 + node0)), e0);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
             c = ep[j];
         }
         if (uint32_t(j) < e) {
-            const NodeKey nk{x0 + uint32_t(j), rid + p.r0, t, p.k0, p.k1};
+            const NodeKey nk{p.x_base + x0 + uint32_t(j), rid + p.r0, t, p.k0, p.k1};
             uint32_t ln, ld;
             node_rate(p.galilean != 0u, a, b, c, p.lam_n, p.lam_d, ln, ld);
             collide_node(a, b, c, nk, p.rk, p.C, ln, ld, err);
@@ -276,7 +278,8 @@ __global__ void k_from_device_form(const uint16_t *__restrict__ B, uint64_t P, u
                                    uint64_t S, const uint64_t *__restrict__ abi_off,
                                    const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
                                    const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
-                                   const uint32_t *__restrict__ rep_id, int stream)
+                                   const uint32_t *__restrict__ rep_id, int stream,
+                                   const uint16_t *__restrict__ halo)
 {
     const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= chunks) return;
@@ -289,9 +292,10 @@ __global__ void k_from_device_form(const uint16_t *__restrict__ B, uint64_t P, u
         if (x < c.L) {
             const uint32_t xr = stream ? (x + 1u == c.L ? 0u : x + 1u) : x;
             const uint32_t xl = stream ? (x == 0u ? c.L - 1u : x - 1u) : x;
-            n[c.a0 + x] = B[c.base + xr];
+            // a block of a larger lattice: its edges' arriving values come from the halo
+            n[c.a0 + x] = (halo && stream && x + 1u == c.L) ? halo[1] : B[c.base + xr];
             n[S + c.a0 + x] = uint16_t(ez[j]);
-            n[2 * S + c.a0 + x] = B[2 * P + c.base + xl];
+            n[2 * S + c.a0 + x] = (halo && stream && x == 0u) ? halo[0] : B[2 * P + c.base + xl];
         }
     }
 }
@@ -303,7 +307,7 @@ __global__ void k_moments(const uint16_t *__restrict__ B, uint64_t P, int32_t *_
                           const uint64_t *__restrict__ rep_off, const uint32_t *__restrict__ rep_L,
                           const uint32_t *__restrict__ chunk_rep, uint64_t chunks,
                           const uint32_t *__restrict__ rep_id, int stream,
-                          unsigned long long *__restrict__ totals)
+                          const uint16_t *__restrict__ halo, unsigned long long *__restrict__ totals)
 {
     const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     long long sn = 0, sj = 0;
@@ -317,7 +321,9 @@ __global__ void k_moments(const uint16_t *__restrict__ B, uint64_t P, int32_t *_
             if (x < c.L) {
                 const uint32_t xr = stream ? (x + 1u == c.L ? 0u : x + 1u) : x;
                 const uint32_t xl = stream ? (x == 0u ? c.L - 1u : x - 1u) : x;
-                const int32_t a = B[c.base + xr], b = int32_t(ez[j]), cc = B[2 * P + c.base + xl];
+                const int32_t a = (halo && stream && x + 1u == c.L) ? halo[1] : B[c.base + xr];
+                const int32_t b = int32_t(ez[j]);
+                const int32_t cc = (halo && stream && x == 0u) ? halo[0] : B[2 * P + c.base + xl];
                 const uint64_t o = c.a0 + x;
                 if (N) N[o] = a + b + cc;
                 if (J) J[o] = cc - a;
@@ -590,24 +596,24 @@ cudaError_t launch_to_device_form(const uint16_t *n, uint64_t S, uint16_t *B, co
 }
 
 cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, const Layout &lay,
-                                    int stream, cudaStream_t s)
+                                    int stream, const uint16_t *halo, cudaStream_t s)
 {
     const uint64_t chunks = lay.P / 8u;
     const uint32_t th = 256;
     k_from_device_form<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
         B, lay.P, n, S, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks,
-        lay.d_rep_id, stream);
+        lay.d_rep_id, stream, halo);
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
-                           unsigned long long *totals, cudaStream_t s)
+                           const uint16_t *halo, unsigned long long *totals, cudaStream_t s)
 {
     const uint64_t chunks = lay.P / 8u;
     const uint32_t th = 256;
     k_moments<<<uint32_t((chunks + th - 1) / th), th, 0, s>>>(
         B, lay.P, N, J, lay.d_abi_off, lay.d_rep_off, lay.d_rep_L, lay.d_chunk_rep, chunks,
-        lay.d_rep_id, stream, totals);
+        lay.d_rep_id, stream, halo, totals);
     return cudaGetLastError();
 }
 

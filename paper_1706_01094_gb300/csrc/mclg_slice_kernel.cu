@@ -299,8 +299,10 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
     // with the vector loads; the others take them from the neighbouring lanes
     const bool own_next = !(lane < 31u && x0 + V < L), own_prev = !(lane > 0u && x0 > 0u);
     uint32_t nxt_own = 0u, prv_own = 0u;
-    if (kStream && own_next) nxt_own = inm[off + (x0 + V < L ? x0 + V : 0u)];
-    if (kStream && own_prev) prv_own = inp[off + (x0 > 0u ? x0 - 1u : L - 1u)];
+    if (kStream && own_next)
+        nxt_own = x0 + V < L ? inm[off + x0 + V] : (kOne && p.halo_in ? p.halo_in[1] : inm[off]);
+    if (kStream && own_prev)
+        prv_own = x0 > 0u ? inp[off + x0 - 1u] : (kOne && p.halo_in ? p.halo_in[0] : inp[off + L - 1u]);
     uint32_t em[V], e0[V], ep[V];
     unpack(__ldcs(reinterpret_cast<const T *>(inm + node0)), em);
     unpack(__ldcs(reinterpret_cast<const T *>(in0 + node0)), e0);
@@ -315,8 +317,8 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
 
     uint32_t err = 0;
     uint32_t om[V], o0[V], op[V];
-    uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, x0, nv, rid + p.r0,
-                                              t, p, tab, om, o0, op, err);
+    uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv,
+                                              rid + p.r0, t, p, tab, om, o0, op, err);
     if (active) {
         T vo;
         pack(om, vo);
@@ -499,8 +501,10 @@ __global__ void __launch_bounds__((W + 1) * 32, kMinBlocks)
         const bool own_next = !(lane < 31u && x0 + V < L), own_prev = !(lane > 0u && x0 > 0u);
         uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
         uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
-        if (kStream && own_next) nxt = x0 + V < L ? uint32_t(sm[xl + V]) : uint32_t(inm[0]);
-        if (kStream && own_prev) prv = x0 > 0u ? uint32_t(sp[int(xl) - 1]) : uint32_t(inp[L - 1u]);
+        if (kStream && own_next)
+            nxt = x0 + V < L ? uint32_t(sm[xl + V]) : uint32_t(p.halo_in ? p.halo_in[1] : inm[0]);
+        if (kStream && own_prev)
+            prv = x0 > 0u ? uint32_t(sp[int(xl) - 1]) : uint32_t(p.halo_in ? p.halo_in[0] : inp[L - 1u]);
 
         const bool active = xl < n;
         const uint32_t nv = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
@@ -509,7 +513,7 @@ __global__ void __launch_bounds__((W + 1) * 32, kMinBlocks)
         // been consumed (arriving right after issuing the shared-memory loads let
         // the next bulk copy overwrite values still in flight)
         uint32_t heavy = slice_vector_phased<V, kNarrow>(
-            em, e0, ep, nxt, prv, kStream, x0, nv, r, t, p, tab, om, o0, op, err, [&]() {
+            em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv, r, t, p, tab, om, o0, op, err, [&]() {
                 __syncwarp();
                 if (lane == 0u) mbar_arrive(&empty[s]);
             });
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_step_heavy(PlainArgs p, Slice
         const uint32_t x = uint32_t(pos - off);
         uint32_t a = p.out[pos], b = p.out[p.P + pos], c = p.out[2 * p.P + pos];
         if (x >= L || a + b + c <= tab.n_max) continue;  // padding, or a table node (scan)
-        const NodeKey nk{x, rid + p.r0, t, p.k0, p.k1};
+        const NodeKey nk{p.x_base + x, rid + p.r0, t, p.k0, p.k1};
         uint32_t ln, ld;
         node_rate(p.galilean != 0u, a, b, c, p.lam_n, p.lam_d, ln, ld);
         collide_node(a, b, c, nk, p.rk, p.C, ln, ld, err);

@@ -22,13 +22,15 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime e
 NO_STREAM = 1
 STATS = 2
 GALILEAN = 4
+HALO = 8
 MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT, MODE_BATCHED = 0, 1, 2, 3
 SAMPLER_SEQUENTIAL, SAMPLER_SLICE = 0, 1
 
 EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
            "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
            "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox",
-           "mclg_moments_noalloc", "mclg_tuning", "mclg_slice_row"]
+           "mclg_moments_noalloc", "mclg_tuning", "mclg_slice_row", "mclg_halo_get",
+           "mclg_halo_put"]
 
 
 class MCLGError(RuntimeError):
@@ -42,7 +44,7 @@ class Params(ctypes.Structure):
                 ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32),
                 ("sampler", ctypes.c_uint32), ("slice_n_max", ctypes.c_uint32),
-                ("kernel_variant", ctypes.c_uint32)]
+                ("kernel_variant", ctypes.c_uint32), ("node_offset", ctypes.c_uint32)]
 
 
 _lib = None
@@ -99,6 +101,10 @@ def load() -> ctypes.CDLL:
         lib.mclg_tuning.restype = st
         lib.mclg_moments_noalloc.argtypes = [P, u64, P, P, P, P]
         lib.mclg_moments_noalloc.restype = st
+        lib.mclg_halo_get.argtypes = [P, P]
+        lib.mclg_halo_get.restype = st
+        lib.mclg_halo_put.argtypes = [P, P]
+        lib.mclg_halo_put.restype = st
         _lib = lib
         return lib
 
@@ -132,18 +138,23 @@ def _stream_ptr(stream):
 
 
 class Lattice:
-    """A handle: `replicas` independent periodic D1Q3 lattices of lengths L."""
+    """A handle: `replicas` independent periodic D1Q3 lattices of lengths L, or
+    (``node_offset`` given) one block of a larger periodic lattice whose edges
+    exchange values with the neighbouring blocks (halo_get / halo_put)."""
 
     def __init__(self, L, seed: int = 1, C: int = 10, lam=(1, 1), flags: int = 0,
                  mode: int = MODE_AUTO, stream=None, first_replica: int = 0,
                  sampler: int = SAMPLER_SEQUENTIAL, slice_n_max: int = 0,
-                 kernel_variant=None):
+                 kernel_variant=None, node_offset=None):
         self._lib = load()
         self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32).reshape(-1))
         self.S = int(self.L.sum())
         self.seed = int(seed)
         kv = 0 if kernel_variant is None else int(kernel_variant) + 1  # None: autotune
-        p = Params(C, lam[0], lam[1], flags, mode, first_replica, sampler, slice_n_max, kv)
+        if node_offset is not None:
+            flags |= HALO
+        p = Params(C, lam[0], lam[1], flags, mode, first_replica, sampler, slice_n_max, kv,
+                   0 if node_offset is None else int(node_offset))
         h = ctypes.c_void_p()
         _check(self._lib.mclg_create(_ptr(self.L), self.L.size, self.seed & (2**64 - 1),
                                      ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),
@@ -196,6 +207,22 @@ class Lattice:
 
     def sync(self):
         _check(self._lib.mclg_sync(self._h), "mclg_sync")
+
+    # -- a block of a larger lattice -------------------------------------------
+    def halo_get(self, out=None):
+        """The two post-collision values leaving the block after the last step:
+        (v = -1 of the first node, v = +1 of the last node)."""
+        if out is None:
+            out = np.zeros(2, dtype=np.uint16)
+        _check(self._lib.mclg_halo_get(self._h, _ptr(out)), "mclg_halo_get")
+        return out
+
+    def halo_put(self, values):
+        """The two values arriving for the next step: (v = +1 into the first node,
+        from the left neighbour; v = -1 into the last node, from the right one)."""
+        if isinstance(values, np.ndarray) or not hasattr(values, "data_ptr"):
+            values = np.ascontiguousarray(np.asarray(values, dtype=np.uint16).reshape(2))
+        _check(self._lib.mclg_halo_put(self._h, _ptr(values)), "mclg_halo_put")
 
     def sync_status(self) -> int:
         return int(self._lib.mclg_sync(self._h))

@@ -18,8 +18,9 @@ PROBE = r"""
 int main(void) {
     printf("size %zu\n", sizeof(mclg_params));
     F(C) F(lambda_num) F(lambda_den) F(flags) F(mode) F(first_replica) F(sampler)
-    F(slice_n_max) F(kernel_variant)
-    printf("NO_STREAM %u\nSTATS %u\nGALILEAN %u\n", MCLG_NO_STREAM, MCLG_STATS, MCLG_GALILEAN);
+    F(slice_n_max) F(kernel_variant) F(node_offset)
+    printf("NO_STREAM %u\nSTATS %u\nGALILEAN %u\nHALO %u\n", MCLG_NO_STREAM, MCLG_STATS,
+           MCLG_GALILEAN, MCLG_HALO);
     printf("MODE_AUTO %u\nMODE_PLAIN %u\nMODE_PERSISTENT %u\nMODE_BATCHED %u\n",
            MCLG_MODE_AUTO, MCLG_MODE_PLAIN, MCLG_MODE_PERSISTENT, MCLG_MODE_BATCHED);
     printf("SAMPLER_SEQUENTIAL %u\nSAMPLER_SLICE %u\n", MCLG_SAMPLER_SEQUENTIAL, MCLG_SAMPLER_SLICE);
@@ -58,7 +59,7 @@ def test_params_struct_layout_matches_header(header_values):
 
 def test_constants_match_header(header_values):
     m = mclg_module()
-    for name in ("NO_STREAM", "STATS", "GALILEAN", "MODE_AUTO", "MODE_PLAIN", "MODE_PERSISTENT",
+    for name in ("NO_STREAM", "STATS", "GALILEAN", "HALO", "MODE_AUTO", "MODE_PLAIN", "MODE_PERSISTENT",
                  "MODE_BATCHED", "SAMPLER_SEQUENTIAL", "SAMPLER_SLICE"):
         assert getattr(m, name) == header_values[name], name
     assert sorted(m.STATUS) == list(range(header_values["status_max"] + 1))
