@@ -200,7 +200,10 @@ uint64_t mclg_time(mclg_handle h);
  * index (register bound), cfg[1] = threads per persistent CTA,
  * cfg[2] = nodes per persistent work unit, cfg[3] = number of persistent work
  * units, cfg[4] = persistent register-bound variant (0, 1, 2 = 1, 2, 3 CTAs of
- * 512 threads per SM), cfg[5] = 0 (reserved). */
+ * 512 threads per SM), cfg[5] = the launch configuration of the slice
+ * sampler's statistics form (MCLG_STATS with MCLG_SAMPLER_SLICE: 0-3 for 4 or
+ * 8 replicas per warp, shared-memory counters updated by load-add-store or by
+ * reductions), else 0. */
 mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6]);
 
 /* Domain decomposition of one periodic lattice (MCLG_HALO handles).  The

@@ -75,6 +75,9 @@ struct mclg_ctx {
     bool halo_ready = false;          // the arriving values of the current time are in d_halo
     bool stepped = false;             // a step has run since the state was set
     uint16_t *d_halo = nullptr;       // [2]: v = +1 into node 0, v = -1 into node L - 1
+    uint32_t *d_stats_from = nullptr; // statistics form of the slice step: first time step
+                                      // whose input field is a sample
+    uint32_t stats_config = 0;        // statistics form: autotuned launch configuration
 };
 
 namespace {
@@ -307,6 +310,10 @@ mclg_status autotune(mclg_ctx *h)
     return MCLG_OK;
 }
 
+bool fused_stats(const mclg_ctx *h);
+cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t ke,
+                           cudaStream_t s, const uint32_t *t_dev);
+
 // Plain-kernel autotuner: time each vector width on the real input, writing
 // into the buffer the next step overwrites anyway (results do not depend on
 // the width), and keep the fastest.
@@ -316,6 +323,35 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
     cudaEvent_t e0, e1;
     MCLG_CK(cudaEventCreate(&e0));
     MCLG_CK(cudaEventCreate(&e1));
+    if (fused_stats(h)) {
+        // the statistics form's configurations, timed with no sample counted
+        // (no time step reaches the threshold); the buffer written is the one the
+        // next step overwrites anyway
+        MCLG_CK(launch_set_time(h->d_stats_from, 0xFFFFFFFFu, h->stream));
+        float best = 1e30f;
+        for (uint32_t v = 0; v < kStatsConfigs; ++v) {
+            h->stats_config = v;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 4; ++rep) {
+                MCLG_CK(cudaEventRecord(e0, h->stream));
+                MCLG_CK(plain_step_seq(h, h->cur, h->t, 0, h->R, h->stream, nullptr));
+                MCLG_CK(cudaEventRecord(e1, h->stream));
+                MCLG_CK(cudaEventSynchronize(e1));
+                float one = 0;
+                MCLG_CK(cudaEventElapsedTime(&one, e0, e1));
+                if (rep > 0) ms = std::min(ms, one);
+            }
+            if (ms < best) {
+                best = ms;
+                h->plain_variant = v;  // reported by mclg_tuning
+            }
+        }
+        h->stats_config = h->plain_variant;
+        h->plain_variant = 0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return MCLG_OK;
+    }
     float best = 1e30f;
     uint32_t best_variant = h->plain_variant;
     const uint16_t *in = h->d_B[h->cur];
@@ -348,25 +384,50 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
     return MCLG_OK;
 }
 
+// Statistics with the slice sampler run in the step kernel's statistics form:
+// the kernel of step t adds its input field n(t) (from t = *d_stats_from on).
+bool fused_stats(const mclg_ctx *h)
+{
+    return (h->prm.flags & MCLG_STATS) && h->prm.sampler == MCLG_SAMPLER_SLICE;
+}
+
+// The statistics partial pass over the field in buffer c (adds one sample of
+// every replica to the batch).
+cudaError_t stats_partial(mclg_ctx *h, int c, cudaStream_t s)
+{
+    return launch_stats_partial(h->d_B[c], h->lay.P, h->L[0], h->R, pad8(h->L[0]),
+                                streaming(h) ? 1 : 0, h->d_stat_partials, h->st.count + 2, s);
+}
+
 // One step of the plain path over internal replicas [kb, ke) from buffer c,
-// plus the statistics of the new field when they are on.  With t_dev set the
-// launches read their time step from the device (t is then an offset).
+// plus the statistics when they are on: of the new field (partial pass after
+// the step), or, in the slice sampler's statistics form, of the input field
+// inside the step kernel.  With t_dev set the launches read their time step
+// from the device (t is then an offset).
 cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t ke,
                            cudaStream_t s, const uint32_t *t_dev)
 {
+    if (fused_stats(h)) {
+        PlainArgs a = plain_args(h, h->d_B[c], h->d_B[c ^ 1], t);
+        a.t_dev = t_dev;
+        a.g_begin = 0;
+        a.g_end = h->lay.P / 8u;
+        a.one_L = h->L[0];
+        StatsArgs sa{h->R, pad8(h->L[0]), h->d_stats_from, h->d_stat_partials, h->st.count + 2,
+                     h->stats_config};
+        return launch_slice_stats(a, h->slice, sa, s);
+    }
     cudaError_t e = plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], t, kb, ke, s, t_dev);
     if (e != cudaSuccess) return e;
-    if (h->prm.flags & MCLG_STATS)
-        e = launch_stats_partial(h->d_B[c ^ 1], h->lay.P, h->L[0], h->R, pad8(h->L[0]),
-                                 streaming(h) ? 1 : 0, h->d_stat_partials, s);
+    if (h->prm.flags & MCLG_STATS) e = stats_partial(h, c ^ 1, s);
     return e;
 }
 
-// Fold the statistics of the last `steps` steps into the running moments.
-cudaError_t stats_merge(mclg_ctx *h, uint64_t steps, cudaStream_t s)
+// Fold the batch of samples accumulated so far into the running moments.
+cudaError_t stats_merge(mclg_ctx *h, cudaStream_t s)
 {
-    if (!(h->prm.flags & MCLG_STATS) || steps == 0) return cudaSuccess;
-    return launch_stats_merge(h->d_stat_partials, h->L[0], steps * h->R, h->st, s);
+    if (!(h->prm.flags & MCLG_STATS)) return cudaSuccess;
+    return launch_stats_merge(h->d_stat_partials, h->L[0], h->st, s);
 }
 
 void drop_graphs(mclg_ctx *h)
@@ -395,7 +456,7 @@ mclg_status capture_graph(mclg_ctx *h, int c, uint32_t kb, uint32_t ke)
         e = plain_step_seq(h, cc, j, kb, ke, h->cap, h->d_t);
         cc ^= 1;
     }
-    if (e == cudaSuccess) e = stats_merge(h, kGraphSteps, h->cap);  // one merge per graph
+    if (e == cudaSuccess) e = stats_merge(h, h->cap);  // one merge per graph
     if (e == cudaSuccess) e = launch_advance_time(h->d_t, kGraphSteps, h->cap);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -416,6 +477,10 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
 {
     uint64_t done = 0;
     const uint64_t groups = n_steps / kGraphSteps;
+    // the statistics form counts the input fields from the second step of the
+    // call on: the first one was counted at the end of the previous call (or is
+    // the field at a reset)
+    if (fused_stats(h)) MCLG_CK(launch_set_time(h->d_stats_from, uint32_t(t + 1), s));
     if (groups > 0) {
         mclg_status st = capture_graph(h, c, kb, ke);
         if (st != MCLG_OK) return st;
@@ -423,12 +488,12 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
         for (uint64_t g = 0; g < groups; ++g) MCLG_CK(cudaGraphLaunch(h->graph[c], s));
         done = groups * kGraphSteps;  // even: the parity of c is unchanged
     }
-    const uint64_t rest = n_steps - done;
     for (; done < n_steps; ++done) {
         MCLG_CK(plain_step_seq(h, c, t + done, kb, ke, s, nullptr));
         c ^= 1;
     }
-    MCLG_CK(stats_merge(h, rest, s));  // every call leaves the statistics merged
+    if (fused_stats(h)) MCLG_CK(stats_partial(h, c, s));  // the call's last field
+    MCLG_CK(stats_merge(h, s));  // every call leaves the statistics merged
     *c_out = c;
     return MCLG_OK;
 }
@@ -673,6 +738,7 @@ void mclg_destroy(mclg_handle h)
     cudaFree(h->st.count);
     cudaFree(h->d_stat_partials);
     cudaFree(h->d_halo);
+    cudaFree(h->d_stats_from);
     delete h;
 }
 
@@ -814,7 +880,8 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
             !alloc((void **)&h->st.mean32c, Lc * 3 * sizeof(float)) ||
             !alloc((void **)&h->st.m2, Lc * 6 * sizeof(float)) ||
             !alloc((void **)&h->st.m2c, Lc * 6 * sizeof(float)) ||
-            !alloc((void **)&h->st.count, 2 * sizeof(unsigned long long)) ||
+            !alloc((void **)&h->st.count, 3 * sizeof(unsigned long long)) ||
+            !alloc((void **)&h->d_stats_from, sizeof(uint32_t)) ||
             !alloc((void **)&h->d_stat_partials, stats_partials_bytes(Lc, replicas)))
             return fail(MCLG_ERR_NOMEM);
         *out = h;
@@ -1028,7 +1095,7 @@ mclg_status mclg_stats_reset(mclg_handle h)
     MCLG_CK(cudaMemsetAsync(h->st.mean32c, 0, Lc * 3 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.m2, 0, Lc * 6 * sizeof(float), h->stream));
     MCLG_CK(cudaMemsetAsync(h->st.m2c, 0, Lc * 6 * sizeof(float), h->stream));
-    MCLG_CK(cudaMemsetAsync(h->st.count, 0, 2 * sizeof(unsigned long long), h->stream));
+    MCLG_CK(cudaMemsetAsync(h->st.count, 0, 3 * sizeof(unsigned long long), h->stream));
     MCLG_CK(cudaMemsetAsync(h->d_stat_partials, 0, stats_partials_bytes(uint32_t(Lc), h->R),
                             h->stream));
     h->stats_count = 0;
@@ -1134,7 +1201,7 @@ mclg_status mclg_tuning(mclg_handle h, uint32_t cfg[6])
 {
     if (!h || !cfg) return MCLG_ERR_ARG;
     cfg[4] = h->tuned ? h->p_variant : 0u;
-    cfg[5] = 0u;
+    cfg[5] = fused_stats(h) && h->plain_tuned ? h->stats_config : 0u;
     const uint32_t vec = h->prm.sampler == MCLG_SAMPLER_SLICE ? slice_variant_vec(h->plain_variant)
                                                                : plain_variant_vec(h->plain_variant);
     cfg[0] = h->plain_tuned ? vec * 100u + h->plain_variant : 0u;

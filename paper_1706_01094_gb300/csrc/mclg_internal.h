@@ -92,8 +92,22 @@ struct StatsBuffers {
     long long *s1, *s2, *snb;   // [L*3], [L*6], [L*9]
     float *mean32, *mean32c;    // [L*3] running means and their compensation
     float *m2, *m2c;            // [L*6] running co-moments and their compensation
-    unsigned long long *count;  // [2]: samples per position, finishing ticket of the merge pass
+    unsigned long long *count;  // [3]: samples per position, finishing ticket of the merge
+                                // pass, samples in the batch not merged yet
 };
+
+// The statistics accumulated by the slice kernel's statistics form (one pass
+// over the state per step: the kernel of step t adds the field it reads, n(t),
+// when t >= *stats_from).
+struct StatsArgs {
+    uint32_t R;                        // replicas, all of length PlainArgs::one_L, ABI order
+    uint64_t stride;                   // node offset between consecutive replicas
+    const uint32_t *stats_from;        // first time step whose input field is a sample
+    unsigned long long *batch;         // [L][18] sums of the batch
+    unsigned long long *batch_count;   // samples in the batch
+    uint32_t config;                   // launch configuration (see launch_slice_stats)
+};
+constexpr uint32_t kStatsConfigs = 4;  // statistics-form launch configurations
 
 cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
 
@@ -136,14 +150,18 @@ cudaError_t launch_from_device_form(const uint16_t *B, uint16_t *n, uint64_t S, 
 cudaError_t launch_moments(const uint16_t *B, int32_t *N, int32_t *J, const Layout &lay, int stream,
                            const uint16_t *halo, unsigned long long *totals, cudaStream_t s);
 size_t stats_partials_bytes(uint32_t L, uint32_t R);
-// Statistics: the partial pass adds one step's exact sums to the batch sums;
-// the merge pass folds a batch of n samples per position (steps x R) into the
-// int64 accumulators and the FP32 running moments and clears the batch.
+// Statistics: the partial pass adds one field's exact sums to the batch sums
+// (and R to the batch's sample count); the merge pass folds the batch into the
+// int64 accumulators and the FP32 running moments and clears it.
 cudaError_t launch_stats_partial(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R,
                                  uint64_t stride, int stream, unsigned long long *batch,
-                                 cudaStream_t s);
-cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, uint64_t n,
-                               const StatsBuffers &st, cudaStream_t s);
+                                 unsigned long long *batch_count, cudaStream_t s);
+cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, const StatsBuffers &st,
+                               cudaStream_t s);
+// One slice-sampler step of every replica with the statistics of its input field
+// (then the heavy-node pass).
+cudaError_t launch_slice_stats(const PlainArgs &p, const SliceTables &tab, const StatsArgs &sa,
+                               cudaStream_t s);
 cudaError_t launch_set_time(uint32_t *t_dev, uint32_t value, cudaStream_t s);
 cudaError_t launch_advance_time(uint32_t *t_dev, uint32_t by, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1, uint32_t *out,

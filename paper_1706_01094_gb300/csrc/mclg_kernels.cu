@@ -361,9 +361,12 @@ constexpr int kStatQ = 18;  // 3 sums + 6 products + 9 neighbour products
 __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restrict__ B, uint64_t P,
                                                        uint32_t L, uint32_t R, uint64_t stride,
                                                        int stream, uint32_t slices,
-                                                       unsigned long long *__restrict__ batch)
+                                                       unsigned long long *__restrict__ batch,
+                                                       unsigned long long *__restrict__ batch_count)
 {
     const uint32_t xl = threadIdx.x & 31u, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        atomicAdd(batch_count, (unsigned long long)R);  // one sample of every replica
     const uint32_t x = blockIdx.x * 32u + xl;
     const uint32_t slice = blockIdx.y;
     const uint32_t r_begin = uint32_t(uint64_t(R) * slice / slices);
@@ -433,13 +436,15 @@ __global__ void __launch_bounds__(256) k_stats_partial(const uint16_t *__restric
 // accumulator and clears it; then one thread per position merges the batch
 // into the FP32 running means and co-moments (Chan et al.), with Kahan
 // compensation, reading the batch from shared memory.  count[0] holds the
-// samples per position so far; count[1] is the blocks' finishing ticket.
+// samples per position so far, count[1] is the blocks' finishing ticket and
+// count[2] the samples in the batch (added by the passes that filled it).
 constexpr uint32_t kMergePositions = 14;  // 14 x 18 = 252 threads per block
 
 __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restrict__ batch,
-                                                     uint32_t L, uint64_t n, StatsBuffers st)
+                                                     uint32_t L, StatsBuffers st)
 {
     __shared__ long long sb[kMergePositions][kStatQ];
+    const uint64_t n = *(volatile unsigned long long *)(st.count + 2);  // samples in this batch
     const uint32_t lp = threadIdx.x / kStatQ, q = threadIdx.x % kStatQ;
     const uint32_t x = blockIdx.x * kMergePositions + lp;
     if (lp < kMergePositions && x < L) {
@@ -453,7 +458,7 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
     }
     __syncthreads();
     const uint32_t xm = blockIdx.x * kMergePositions + threadIdx.x;
-    if (threadIdx.x < kMergePositions && xm < L) {
+    if (threadIdx.x < kMergePositions && xm < L && n > 0u) {
         const long long *acc = sb[threadIdx.x];
         const float Rb = float(n);  // samples per position in this batch
         const float Ma = float(*st.count);  // samples per position before this batch
@@ -489,6 +494,7 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
         if (atomicAdd(st.count + 1, 1ull) == gridDim.x - 1u) {
             st.count[0] += n;
             st.count[1] = 0ull;
+            st.count[2] = 0ull;
             __threadfence();
         }
     }
@@ -632,18 +638,18 @@ size_t stats_partials_bytes(uint32_t L, uint32_t R)
 
 cudaError_t launch_stats_partial(const uint16_t *B, uint64_t P, uint32_t L, uint32_t R,
                                  uint64_t stride, int stream, unsigned long long *batch,
-                                 cudaStream_t s)
+                                 unsigned long long *batch_count, cudaStream_t s)
 {
     const uint32_t slices = stats_slices(R);
     const dim3 grid((L + 31) / 32, slices);
-    k_stats_partial<<<grid, 256, 0, s>>>(B, P, L, R, stride, stream, slices, batch);
+    k_stats_partial<<<grid, 256, 0, s>>>(B, P, L, R, stride, stream, slices, batch, batch_count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, uint64_t n,
-                               const StatsBuffers &st, cudaStream_t s)
+cudaError_t launch_stats_merge(unsigned long long *batch, uint32_t L, const StatsBuffers &st,
+                               cudaStream_t s)
 {
-    k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, n, st);
+    k_stats_merge<<<(L + kMergePositions - 1) / kMergePositions, 256, 0, s>>>(batch, L, st);
     return cudaGetLastError();
 }
 

@@ -555,6 +555,149 @@ static cudaError_t launch_slice_ws_v(const PlainArgs &p, const SliceTables &tab,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Statistics form (MCLG_STATS with the slice sampler): one pass per step that
+// both steps the replicas and adds the statistics of the field it reads,
+// n(x, t) (Sec. V: sums of n_i, n_i n_j at a node and n_i(x) n_j(x + 1)), so
+// the state is not read a second time.  A CTA of 8 warps takes 64 positions
+// of KR x 8 replicas: warp w steps replicas w, w + 8, ... (2 nodes per lane,
+// as k_step_slice does) and adds each node's 18 quantities to its lane's
+// 32-bit counters in shared memory (exact while every value is below 2^14 and
+// KR <= 16: 16 products below 2^28 fit 32 bits; a node with a larger value
+// adds its quantities to the global 64-bit sums at once); at the end the CTA
+// folds its 8 warps' counters into the batch sums with one 64-bit atomic per
+// position and quantity.  The kernel of step t adds its input only when
+// t >= *stats_from (the library's last call ended with n(t) already added, or
+// n(t) is the field at a reset): every field after a reset is counted once.
+// ---------------------------------------------------------------------------
+constexpr int kStatQty = 18;  // 3 sums + 6 same-node products + 9 neighbour products
+
+__device__ __forceinline__ void node_quantities(uint32_t a, uint32_t b, uint32_t c, uint32_t a1,
+                                                uint32_t b1, uint32_t c1, uint32_t (&q)[kStatQty])
+{
+    q[0] = a; q[1] = b; q[2] = c;
+    q[3] = a * a; q[4] = a * b; q[5] = a * c; q[6] = b * b; q[7] = b * c; q[8] = c * c;
+    q[9] = a * a1; q[10] = a * b1; q[11] = a * c1;
+    q[12] = b * a1; q[13] = b * b1; q[14] = b * c1;
+    q[15] = c * a1; q[16] = c * b1; q[17] = c * c1;
+}
+
+template <int KR, bool kRed, bool kNarrow, bool kStream>
+__global__ void __launch_bounds__(256) k_step_slice_stats(PlainArgs p, SliceTables tab, StatsArgs sa)
+{
+    static_assert(KR >= 1 && KR <= 16, "32-bit counters hold at most 16 products below 2^28");
+    constexpr int V = 2;
+    __shared__ uint32_t cnt[8][V * kStatQty][32];  // per warp, (node, quantity), lane
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t L = p.one_L, Pn = (L + 7u) & ~7u;
+    const uint32_t x0 = blockIdx.x * 64u + lane * V;       // replica-local first node of the lane
+    const bool inside = x0 < Pn;
+    const uint32_t xv = inside ? x0 : Pn - V;              // lanes past the replica mirror its end
+    const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
+    const bool acc = t >= *sa.stats_from;
+#pragma unroll
+    for (int k = 0; k < V * kStatQty; ++k) cnt[warp][k][lane] = 0u;
+    uint32_t err = 0;
+    const uint16_t *__restrict__ inm = p.in;
+    const uint16_t *__restrict__ in0 = p.in + p.P;
+    const uint16_t *__restrict__ inp = p.in + 2 * p.P;
+    for (int k = 0; k < KR; ++k) {
+        const uint32_t r = blockIdx.y * (8u * KR) + warp + 8u * uint32_t(k);
+        if (r >= sa.R) break;  // the same for the whole warp
+        const uint64_t off = uint64_t(r) * sa.stride, node0 = off + xv;
+        const bool own_next = !(lane < 31u && xv + V < L), own_prev = !(lane > 0u && xv > 0u);
+        uint32_t nxt_own = 0u, prv_own = 0u;
+        if (kStream && own_next) nxt_own = inm[off + (xv + V < L ? xv + V : 0u)];
+        if (kStream && own_prev) prv_own = inp[off + (xv > 0u ? xv - 1u : L - 1u)];
+        uint32_t em[V], e0[V], ep[V];
+        unpack(__ldcs(reinterpret_cast<const uint32_t *>(inm + node0)), em);
+        unpack(__ldcs(reinterpret_cast<const uint32_t *>(in0 + node0)), e0);
+        unpack(__ldcs(reinterpret_cast<const uint32_t *>(inp + node0)), ep);
+        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
+        uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
+        if (kStream && own_next) nxt = nxt_own;
+        if (kStream && own_prev) prv = prv_own;
+        const uint32_t nv = (!inside || xv >= L) ? 0u : (L - xv < uint32_t(V) ? L - xv : uint32_t(V));
+        // the input field n(x, t) of the lane's nodes (the values the step collides)
+        uint32_t na[V], nb[V], nc[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            na[j] = kStream ? ((uint32_t(j) + 1u < nv) ? em[(j + 1) % V] : nxt) : em[j];
+            nb[j] = e0[j];
+            nc[j] = kStream ? ((j > 0) ? ep[(j + V - 1) % V] : prv) : ep[j];
+        }
+        uint32_t om[V], o0[V], op[V];
+        uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, p.x_base + xv, nv,
+                                                  r + p.r0, t, p, tab, om, o0, op, err);
+        if (inside) {
+            __stcs(reinterpret_cast<uint32_t *>(p.out + node0), om[0] | (om[1] << 16));
+            __stcs(reinterpret_cast<uint32_t *>(p.out + p.P + node0), o0[0] | (o0[1] << 16));
+            __stcs(reinterpret_cast<uint32_t *>(p.out + 2 * p.P + node0), op[0] | (op[1] << 16));
+        }
+        if (!inside) heavy = 0u;
+        list_heavy<V>(heavy, node0, lane, tab);
+        if (!acc) continue;
+        // the right neighbour of the lane's last node: the next lane's first node,
+        // or (at the end of a warp or of the replica) read from the input field
+        uint32_t a1 = __shfl_down_sync(0xFFFFFFFFu, na[0], 1);
+        uint32_t b1 = __shfl_down_sync(0xFFFFFFFFu, nb[0], 1);
+        uint32_t c1 = __shfl_down_sync(0xFFFFFFFFu, nc[0], 1);
+        if (nv > 0u && (lane == 31u || xv + nv >= L)) {
+            const uint32_t y = xv + nv < L ? xv + nv : 0u;   // node after the last valid one
+            const uint32_t yr = kStream ? (y + 1u < L ? y + 1u : 0u) : y;
+            const uint32_t yl = kStream ? (y > 0u ? y - 1u : L - 1u) : y;
+            a1 = inm[off + yr];
+            b1 = in0[off + y];
+            c1 = inp[off + yl];
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (uint32_t(j) >= nv) break;
+            const bool last = uint32_t(j) + 1u == nv;
+            uint32_t q[kStatQty];
+            node_quantities(na[j], nb[j], nc[j], last ? a1 : na[j + 1 < V ? j + 1 : j],
+                            last ? b1 : nb[j + 1 < V ? j + 1 : j],
+                            last ? c1 : nc[j + 1 < V ? j + 1 : j], q);
+            const uint32_t big = na[j] | nb[j] | nc[j] | (last ? (a1 | b1 | c1) : 0u) |
+                                 (j + 1 < V ? na[j + 1] | nb[j + 1] | nc[j + 1] : 0u);
+            if (big < (1u << 14)) {
+#pragma unroll
+                for (int m = 0; m < kStatQty; ++m) {  // the lane's own counter: no contention
+                    if (kRed) atomicAdd(&cnt[warp][j * kStatQty + m][lane], q[m]);
+                    else cnt[warp][j * kStatQty + m][lane] += q[m];
+                }
+            } else {
+                // values of 2^14 or more: exact 64-bit products straight into the batch
+                const uint64_t v[3] = {na[j], nb[j], nc[j]};
+                const int jn = j + 1 < V ? j + 1 : j;  // the next node when it is this lane's
+                const uint64_t w[3] = {last ? a1 : na[jn], last ? b1 : nb[jn], last ? c1 : nc[jn]};
+                unsigned long long *dst = sa.batch + uint64_t(xv + j) * kStatQty;
+                int m = 0;
+                for (int i = 0; i < 3; ++i) atomicAdd(dst + m++, v[i]);
+                for (int i = 0; i < 3; ++i)
+                    for (int i2 = i; i2 < 3; ++i2) atomicAdd(dst + m++, v[i] * v[i2]);
+                for (int i = 0; i < 3; ++i)
+                    for (int i2 = 0; i2 < 3; ++i2) atomicAdd(dst + m++, v[i] * w[i2]);
+            }
+        }
+    }
+    flag_error(p.err, err);
+    if (!acc) return;
+    __syncthreads();
+    // fold the 8 warps' counters: item (node j, quantity m, lane) per thread
+    for (uint32_t it = threadIdx.x; it < uint32_t(V * kStatQty) * 32u; it += blockDim.x) {
+        const uint32_t l = it & 31u, jm = it >> 5, j = jm / kStatQty, m = jm % kStatQty;
+        const uint32_t x = blockIdx.x * 64u + l * V + j;
+        if (x >= L) continue;
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += cnt[w][jm][l];
+        if (sum) atomicAdd(sa.batch + uint64_t(x) * kStatQty + m, sum);
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        atomicAdd(sa.batch_count, (unsigned long long)sa.R);  // one sample of every replica
+}
+
 // The sequential pass over the step's heavy nodes (see above).  Reads the
 // table kernel's output, where heavy nodes still hold their pre-collision
 // state, and overwrites them with their sequential collisions.  The last CTA
@@ -665,6 +808,42 @@ cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, c
     if (e != cudaSuccess) return e;
     if (one) k_step_heavy<true><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
     else k_step_heavy<false><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
+    return cudaGetLastError();
+}
+
+}  // namespace mclg
+
+namespace mclg {
+
+template <int KR, bool kRed>
+static void launch_slice_stats_v(const PlainArgs &p, const SliceTables &tab, const StatsArgs &sa,
+                                 cudaStream_t s)
+{
+    const uint32_t Pn = (p.one_L + 7u) & ~7u;
+    const dim3 grid((Pn + 63u) / 64u, (sa.R + 8u * KR - 1u) / (8u * KR));
+    const bool narrow = tab.guide_narrow != 0u, stream = p.stream != 0u;
+    if (narrow && stream) k_step_slice_stats<KR, kRed, true, true><<<grid, 256, 0, s>>>(p, tab, sa);
+    else if (narrow) k_step_slice_stats<KR, kRed, true, false><<<grid, 256, 0, s>>>(p, tab, sa);
+    else if (stream) k_step_slice_stats<KR, kRed, false, true><<<grid, 256, 0, s>>>(p, tab, sa);
+    else k_step_slice_stats<KR, kRed, false, false><<<grid, 256, 0, s>>>(p, tab, sa);
+}
+
+// Statistics-form configurations (replicas per warp, shared-memory counter
+// updates as reductions or as load-add-store), chosen by the autotuner.
+cudaError_t launch_slice_stats(const PlainArgs &p, const SliceTables &tab, const StatsArgs &sa,
+                               cudaStream_t s)
+{
+    switch (sa.config) {
+    case 0: launch_slice_stats_v<4, false>(p, tab, sa, s); break;
+    case 1: launch_slice_stats_v<8, false>(p, tab, sa, s); break;
+    case 2: launch_slice_stats_v<4, true>(p, tab, sa, s); break;
+    default: launch_slice_stats_v<8, true>(p, tab, sa, s); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the heavy-node pass runs over the whole range of replicas
+    if (p.g_end == p.g_begin) return cudaSuccess;
+    k_step_heavy<false><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
     return cudaGetLastError();
 }
 

@@ -232,7 +232,8 @@ class Lattice:
         _check(self._lib.mclg_tuning(self._h, _ptr(cfg)), "mclg_tuning")
         return {"plain_nodes_per_thread": int(cfg[0]) // 100, "plain_variant": int(cfg[0]) % 100,
                 "persistent_threads": int(cfg[1]), "persistent_unit_nodes": int(cfg[2]),
-                "persistent_units": int(cfg[3]), "persistent_variant": int(cfg[4])}
+                "persistent_units": int(cfg[3]), "persistent_variant": int(cfg[4]),
+                "stats_config": int(cfg[5])}
 
     @property
     def t(self) -> int:

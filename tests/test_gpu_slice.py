@@ -165,3 +165,42 @@ def test_warp_specialised_ring_wraps_many_times(variant):
     got = run_slice(L, 17, n0, 40, 2, kernel_variant=variant)
     bad = np.nonzero((got != want).any(axis=0))[0]
     assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
+
+
+@pytest.mark.parametrize("Lc,R,flags,dense", [(100, 37, 0, False), (33, 5, 0, False),
+                                              (1, 3, 0, False), (70, 9, mclg.NO_STREAM, False),
+                                              (64, 33, 0, False), (40, 11, 0, True)])
+def test_slice_statistics_form_exact_sums(Lc, R, flags, dense):
+    """The slice step's statistics form (the step kernel adds the field it reads):
+    every field after a reset counted once over calls of 5, 33 and 1 steps (graph
+    replays among them) and across a reset; tiles with empty positions, ragged
+    replica counts, collide-only runs, and values of 2^14 or more (64-bit path)."""
+    L = np.full(R, Lc, dtype=np.uint32)
+    n0 = workloads.random_state(L, 12.0, seed=Lc + R)
+    if dense:
+        n0[:, 3] = [20000, 17000, 19000]
+        n0[:, Lc + 7] = [16384, 300, 16500]
+    oflags = oracle.FLAG_NO_STREAM if flags & mclg.NO_STREAM else 0
+    ref = oracle.Stats(Lc, R)
+    n, t = n0, 0
+    with mclg.Lattice(L, seed=6, flags=mclg.STATS | flags, sampler=SLICE) as lat:
+        lat.set_state(n0, t=0)
+        lat.stats_reset()
+        for steps in (5, 33, 1, "reset", 4):
+            if steps == "reset":
+                lat.stats_reset()
+                ref = oracle.Stats(Lc, R)
+                continue
+            lat.step(steps)
+            for _ in range(steps):
+                n, err = oracle.slice_step(L, 6, n, t, 1, flags=oflags)
+                assert err == 0
+                ref.accumulate(n)
+                t += 1
+            st = lat.stats_read()
+            assert st["count"] == ref.count
+            assert np.array_equal(st["s1"], ref.s1)
+            assert np.array_equal(st["s2"], ref.s2)
+            assert np.array_equal(st["snb"], ref.snb)
+        got, _ = lat.get_state()
+    assert np.array_equal(got, n)
