@@ -97,7 +97,8 @@ typedef enum {
  *               offsets, Q == F[d'] reported as MCLG_ERR_SAMPLER.  Tables of F
  *               are built exactly (big integers) on the host for masses up to
  *               slice_n_max; heavier nodes take the SEQUENTIAL decisions.
- *               Requires C <= 10; runs in the plain and batched modes. */
+ *               Requires C <= 10; runs in every mode (AUTO takes the
+ *               per-step kernel, MCLG_MODE_PERSISTENT the persistent one). */
 #define MCLG_SAMPLER_SEQUENTIAL 0u
 #define MCLG_SAMPLER_SLICE 1u
 

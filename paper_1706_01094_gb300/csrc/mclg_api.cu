@@ -236,6 +236,8 @@ PersistentArgs persistent_args(const mclg_ctx *h, const uint16_t *in, uint16_t *
     a.rk = make_round_keys(h->seed);
     a.unit_counter = h->d_unit_counter;
     a.variant = h->p_variant;
+    a.slice = h->prm.sampler == MCLG_SAMPLER_SLICE ? 1u : 0u;
+    a.tab = h->slice;
     return a;
 }
 
@@ -564,8 +566,12 @@ uint32_t effective_mode(const mclg_ctx *h)
 {
     if (h->halo) return MCLG_MODE_PLAIN;       // one block, edges exchanged every step
     if (h->prm.flags & MCLG_STATS) return 3u;  // batched plain: state in HBM after each step
-    if (h->prm.sampler == MCLG_SAMPLER_SLICE)  // the slice kernel has no persistent form
-        return (h->prm.mode == MCLG_MODE_PLAIN || h->R == 1) ? MCLG_MODE_PLAIN : 3u;
+    if (h->prm.sampler == MCLG_SAMPLER_SLICE) {
+        // AUTO: the per-step slice kernel (the persistent form only on request)
+        if (h->prm.mode == MCLG_MODE_PLAIN || h->R == 1) return MCLG_MODE_PLAIN;
+        if (h->prm.mode == MCLG_MODE_PERSISTENT && h->n_small > 0) return MCLG_MODE_PERSISTENT;
+        return 3u;
+    }
     if (h->prm.mode == MCLG_MODE_PLAIN) return MCLG_MODE_PLAIN;
     if (h->prm.mode == MCLG_MODE_PERSISTENT) return MCLG_MODE_PERSISTENT;
     if (h->prm.mode == 3u) return 3u;

@@ -68,6 +68,21 @@ struct Unit {
     uint32_t rep_begin, rep_end;  // internal replica range
 };
 
+struct SliceTables {
+    uint32_t n_max;             // rows cover 2 <= N <= n_max
+    const uint32_t *rowstart;   // [(n_max + 1)^2]
+    // [rows][kSliceBuckets]: bits 0-4 the number of entries below the bucket,
+    // bits 5-6 min(entries inside it, 3), bits 8-15 the next 8 bits (56..48)
+    // of the entry when it is the only one inside
+    const uint16_t *guide;
+    const unsigned long long *secondary;  // [rows][kSliceRowU64]
+    // nodes heavier than n_max, left for the sequential pass of the same step
+    unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
+    uint32_t *heavy_ctl;            // {count, overflow, blocks done}, zero between steps
+    uint32_t heavy_cap;
+    uint32_t guide_narrow;          // 1: every guide index fits 32 bits (rows < 2^32 / buckets)
+};
+
 struct PersistentArgs {
     const uint16_t *in;
     uint16_t *out;
@@ -85,6 +100,8 @@ struct PersistentArgs {
     uint32_t stream;  // 1: pull-stream before colliding, 0: collide only
     uint32_t galilean; // 1: per-node rate lambda / sqrt(1 + 3 u^2) (galilean_q)
     uint32_t r0;      // random-stream index of replica id 0
+    uint32_t slice;   // 1: the slice sampler (tables below, sequential draws beyond them)
+    SliceTables tab;
     RoundKeys rk;     // Philox round keys of the seed
 };
 
@@ -116,20 +133,6 @@ uint64_t slice_rows(uint32_t n_max);
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d, bool galilean,
                         std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
                         std::vector<uint64_t> &secondary);
-struct SliceTables {
-    uint32_t n_max;             // rows cover 2 <= N <= n_max
-    const uint32_t *rowstart;   // [(n_max + 1)^2]
-    // [rows][kSliceBuckets]: bits 0-4 the number of entries below the bucket,
-    // bits 5-6 min(entries inside it, 3), bits 8-15 the next 8 bits (56..48)
-    // of the entry when it is the only one inside
-    const uint16_t *guide;
-    const unsigned long long *secondary;  // [rows][kSliceRowU64]
-    // nodes heavier than n_max, left for the sequential pass of the same step
-    unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
-    uint32_t *heavy_ctl;            // {count, overflow, blocks done}, zero between steps
-    uint32_t heavy_cap;
-    uint32_t guide_narrow;          // 1: every guide index fits 32 bits (rows < 2^32 / buckets)
-};
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
 constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass (usually empty)
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);

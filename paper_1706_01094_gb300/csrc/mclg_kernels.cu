@@ -19,6 +19,7 @@
 
 #include "mclg_device.cuh"
 #include "mclg_internal.h"
+#include "mclg_slice.cuh"
 
 namespace mclg {
 
@@ -124,9 +125,12 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
 // most `cap` padded nodes, largest first) from an atomic counter and keeps a
 // unit in shared memory for all n_steps steps.  Two shared buffers alternate;
 // one barrier per step.  Each thread updates node pairs (2i, 2i+1), which never
-// straddle a replica because replicas start on multiples of 8 nodes.
+// straddle a replica because replicas start on multiples of 8 nodes.  kSlice:
+// the slice sampler (one table draw per node for masses up to the tables'
+// n_max, the node pair sharing one Philox block; the sequential draws above
+// it), with the tables' indices in 32 bits when kNarrow.
 // ---------------------------------------------------------------------------
-template <int kMinBlocks>
+template <int kMinBlocks, bool kSlice, bool kNarrow>
 __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_persistent(PersistentArgs p)
 {
     const bool kStream = p.stream != 0u;
@@ -195,10 +199,22 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_pers
                 const NodeKey nk0{x, rid, t, p.k0, p.k1};
                 const NodeKey nk1{x + 1u, rid, t, p.k0, p.k1};
                 uint32_t ln, ld;
-                node_rate(p.galilean != 0u, a0, b0, c0, p.lam_n, p.lam_d, ln, ld);
-                collide_node(a0, b0, c0, nk0, p.rk, p.C, ln, ld, err);
-                node_rate(p.galilean != 0u, a1, b1, c1, p.lam_n, p.lam_d, ln, ld);
-                collide_node(a1, b1, c1, nk1, p.rk, p.C, ln, ld, err);
+                bool seq0 = true, seq1 = true;
+                if (kSlice) {
+                    // x is even: the pair's Philox block, words (0, 1) and (2, 3)
+                    uint32_t w0 = x >> 1, w1 = rid, w2 = t, w3 = kPurposeSlice << 28;
+                    philox4x32_10(w0, w1, w2, w3, p.rk);
+                    seq0 = slice_node<kNarrow>(a0, b0, c0, w0, w1, p.tab, p.C, err);
+                    seq1 = slice_node<kNarrow>(a1, b1, c1, w2, w3, p.tab, p.C, err);
+                }
+                if (seq0) {
+                    node_rate(p.galilean != 0u, a0, b0, c0, p.lam_n, p.lam_d, ln, ld);
+                    collide_node(a0, b0, c0, nk0, p.rk, p.C, ln, ld, err);
+                }
+                if (seq1) {
+                    node_rate(p.galilean != 0u, a1, b1, c1, p.lam_n, p.lam_d, ln, ld);
+                    collide_node(a1, b1, c1, nk1, p.rk, p.C, ln, ld, err);
+                }
                 *reinterpret_cast<uint32_t *>(om + i) = a0 | (a1 << 16);
                 *reinterpret_cast<uint32_t *>(oz + i) = b0 | (b1 << 16);
                 *reinterpret_cast<uint32_t *>(op + i) = c0 | (c1 << 16);
@@ -561,21 +577,23 @@ static cudaError_t launch_persistent_v(const PersistentArgs &p, uint32_t n_units
                                        cudaStream_t s)
 {
     const size_t smem = persistent_smem_bytes(p.cap);
-    cudaError_t e = cudaFuncSetAttribute(k_step_persistent<kMinBlocks>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    auto kern = !p.slice ? k_step_persistent<kMinBlocks, false, false>
+                         : (p.tab.guide_narrow ? k_step_persistent<kMinBlocks, true, true>
+                                               : k_step_persistent<kMinBlocks, true, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // as many CTAs as can be resident at once; they pull the units
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<kMinBlocks>,
-                                                           int(threads), smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, int(threads), smem)) !=
+        cudaSuccess)
         return e;
     const uint32_t resident = uint32_t(std::max(1, sms * std::max(per_sm, 1)));
     PersistentArgs a = p;
     a.n_units = n_units;
     if ((e = cudaMemsetAsync(a.unit_counter, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_step_persistent<kMinBlocks><<<std::min(n_units, resident), threads, smem, s>>>(a);
+    kern<<<std::min(n_units, resident), threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

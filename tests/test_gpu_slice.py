@@ -204,3 +204,37 @@ def test_slice_statistics_form_exact_sums(Lc, R, flags, dense):
             assert np.array_equal(st["snb"], ref.snb)
         got, _ = lat.get_state()
     assert np.array_equal(got, n)
+
+
+@pytest.mark.parametrize("flags", [0, mclg.NO_STREAM, mclg.GALILEAN])
+def test_slice_persistent_kernel_bit_exact(flags):
+    """The persistent kernel with the slice sampler (table draws on chip for
+    masses up to n_max, the sequential draws above), on a ragged batch with
+    replicas beyond a work unit (stepped beside it) and heavy nodes."""
+    L = [64, 1, 37, 128, 9, 1024, 5, 4099, 300, 16391, 33]
+    n0 = workloads.random_state(L, 18.0, seed=flags + 1)
+    n0[:, 70] = [150, 100, 120]                  # a mass beyond the tables at node 70
+    oflags = (oracle.FLAG_NO_STREAM if flags & mclg.NO_STREAM else 0) | \
+        (oracle.FLAG_GALILEAN if flags & mclg.GALILEAN else 0)
+    for n_max in (256, 60):
+        want, err = oracle.slice_step(L, 23, n0, 9, 70, flags=oflags, n_max=n_max)
+        assert err == 0
+        got = run_slice(L, 23, n0, 9, 70, mode=mclg.MODE_PERSISTENT, flags=flags,
+                        slice_n_max=n_max)
+        assert np.array_equal(got, want), n_max
+
+
+def test_slice_persistent_full_size_batch_prefix():
+    """The 4096 x 1024 batch (rho per replica up to 500: many masses beyond the
+    tables) with the slice sampler in the persistent kernel, 10 steps, every node."""
+    wl = workloads.batched()
+    n0, err = oracle.init(wl.L, wl.seed, wl.rho, wl.u)
+    assert err == 0
+    want, err = oracle.slice_step(wl.L, wl.seed, n0, 0, 10)
+    assert err == 0
+    with mclg.Lattice(wl.L, seed=wl.seed, sampler=SLICE, mode=mclg.MODE_PERSISTENT) as lat:
+        lat.set_state(n0)
+        lat.step(10)
+        got, _ = lat.get_state()
+    bad = np.nonzero((got != want).any(axis=0))[0]
+    assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
