@@ -84,6 +84,16 @@ def _load():
             lib.orc_block_collide.restype = i32
             lib.orc_block_stream.argtypes = [u32, P, P, P]
             lib.orc_block_stream.restype = None
+            lib.orc2_collision_count.restype = i32
+            lib.orc2_collision.argtypes = [i32, P]
+            lib.orc2_outcomes.argtypes = [i32, i32, P, u32, P, P]
+            lib.orc2_outcomes.restype = i32
+            lib.orc2_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
+            lib.orc2_init.argtypes = [u32, u32, u32, u64, P, P, P, P, u32]
+            lib.orc2_init.restype = i32
+            lib.orc2_step.argtypes = [u32, u32, u32, u64, u32, P, u32, u32, P, u64, u64, u32]
+            lib.orc2_step.restype = i32
+            lib.orc2_moments.argtypes = [u64, P, P, P, P, P]
             lib.orc_set_threads.argtypes = [i32]
             lib.orc_set_threads.restype = i32
             lib.orc_threads.argtypes = []
@@ -286,3 +296,78 @@ class Block:
     def stream(self, incoming) -> None:
         inc = np.ascontiguousarray(np.asarray(incoming, dtype=np.uint16).reshape(2))
         _load().orc_block_stream(self.Lb, _ptr(self.post), _ptr(inc), _ptr(self.n))
+
+
+# ---------------------------------------------------------------------- D2Q9 ---
+# Velocities 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (-1,0), 4 = (0,-1), 5 = (1,1),
+# 6 = (-1,1), 7 = (-1,-1), 8 = (1,-1); rates lambda_1 .. lambda_9 numbered as in
+# Eq. D2Q9MOmega.  The paper's simulation rates (Sec. IV.B): 15/128, 1/4 (x6),
+# 1/8, 18/144.
+D2Q9_VX = (0, 1, 0, -1, 0, 1, -1, -1, 1)
+D2Q9_VY = (0, 0, 1, 0, -1, 1, 1, -1, -1)
+D2Q9_PAPER_LAMBDA = ((15, 32, 32, 32, 32, 32, 32, 16, 16), 128)
+
+
+def _lam2(lam):
+    num = np.ascontiguousarray(np.asarray(lam[0], dtype=np.uint32).reshape(9))
+    return num, int(lam[1])
+
+
+def d2q9_collisions():
+    """The 30 binary collisions [(pair A, pair B, class)] of the oracle's table."""
+    lib = _load()
+    out = []
+    buf = np.zeros(5, dtype=np.int32)
+    for k in range(lib.orc2_collision_count()):
+        lib.orc2_collision(k, _ptr(buf))
+        out.append(((int(buf[0]), int(buf[1])), (int(buf[2]), int(buf[3])), int(buf[4])))
+    return out
+
+
+def d2q9_outcomes(s1: int, s2: int, lam=D2Q9_PAPER_LAMBDA):
+    """[(target pair, numerator)] of a pick of velocities (s1, s2); numerators over
+    128 * lambda_den."""
+    num, den = _lam2(lam)
+    targets = np.zeros(8, dtype=np.int32)
+    nums = np.zeros(4, dtype=np.uint64)
+    n = _load().orc2_outcomes(s1, s2, _ptr(num), den, _ptr(targets), _ptr(nums))
+    return [((int(targets[2 * k]), int(targets[2 * k + 1])), int(nums[k])) for k in range(n)]
+
+
+def d2q9_feq(rho: float, ux: float, uy: float) -> np.ndarray:
+    """Entropic D2Q9 equilibrium of Eq. D2Q9eqdist."""
+    f = np.zeros(9, dtype=np.float64)
+    _load().orc2_feq(float(rho), float(ux), float(uy), _ptr(f))
+    return f
+
+
+def d2q9_init(Lx: int, Ly: int, R: int, seed: int, rho, ux, uy, first_replica: int = 0):
+    S = Lx * Ly * R
+    args = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)) for a in (rho, ux, uy)]
+    if any(a.size != S for a in args):
+        raise ValueError("rho, ux, uy need one value per node")
+    n = np.zeros((9, S), dtype=np.uint16)
+    err = _load().orc2_init(Lx, Ly, R, seed & (2**64 - 1), *[_ptr(a) for a in args], _ptr(n),
+                            first_replica)
+    return n, int(err)
+
+
+def d2q9_step(Lx: int, Ly: int, R: int, seed: int, n, t0: int, n_steps: int, C: int = 10,
+              lam=D2Q9_PAPER_LAMBDA, flags: int = 0, first_replica: int = 0):
+    """D2Q9 time steps (the paper's particle-pick algorithm with exact integer
+    draws); n is [9, R Lx Ly].  Returns (n, error bits)."""
+    S = Lx * Ly * R
+    n = np.ascontiguousarray(np.array(n, dtype=np.uint16, copy=True).reshape(9, S))
+    num, den = _lam2(lam)
+    err = _load().orc2_step(Lx, Ly, R, seed & (2**64 - 1), C, _ptr(num), den, flags, _ptr(n), t0,
+                            n_steps, first_replica)
+    return n, int(err)
+
+
+def d2q9_moments(n):
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.uint16))
+    S = n.shape[1]
+    rho, jx, jy = (np.zeros(S, dtype=np.int32) for _ in range(3))
+    tot = np.zeros(3, dtype=np.int64)
+    _load().orc2_moments(S, _ptr(n), _ptr(rho), _ptr(jx), _ptr(jy), _ptr(tot))
+    return rho, jx, jy, tot

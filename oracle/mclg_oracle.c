@@ -45,6 +45,14 @@
  *                     matrix (N <= 10, and N = 150 by propagated fractions);
  *                     one-step law by chi-square; invariants; n_max below
  *                     every mass reduces it to orc_step bit for bit.
+ *   orc_block_*       pinned: blocks stitched together equal orc_step /
+ *                     orc_slice_step of the whole lattice (gloo ranks too).
+ *   orc2_* (D2Q9)     pinned: the collision table against brute-force
+ *                     enumeration and its symmetry classes; the linearised
+ *                     operator against the paper's printed Eq. D2Q9MOmega;
+ *                     detailed balance of the product Poisson law (N <= 5);
+ *                     one-collision law by chi-square; conservation; pure
+ *                     streaming; Eq. D2Q9eqdist against the H minimiser.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1001,5 +1009,359 @@ void orc_block_stream(uint32_t Lb, const uint16_t *post, const uint16_t in[2], u
         n[y] = y + 1 < Lb ? post[y + 1] : in[1];                          /* v = -1 from the right */
         n[Lb + y] = post[Lb + y];                                         /* v = 0 stays */
         n[2 * (uint64_t)Lb + y] = y > 0 ? post[2 * (uint64_t)Lb + y - 1] : in[0]; /* v = +1 from the left */
+    }
+}
+
+/* ======================================================================== */
+/* D2Q9 (Sec. II.B, III.B, IV.B): velocities v = (vx, vy), vx, vy in        */
+/* {-1, 0, 1}, numbered 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (-1,0),        */
+/* 4 = (0,-1), 5 = (1,1), 6 = (-1,1), 7 = (-1,-1), 8 = (1,-1); weights       */
+/* w = 4/9, 1/9 (1-4), 1/36 (5-8), products of the D1Q3 weights.            */
+/*                                                                          */
+/* Binary collisions: every pair of unordered velocity pairs {A, B} with the */
+/* same total momentum, grouped into the nine equivalence classes of Sec.   */
+/* III.B under the rotations and reflections of the square.  Numbering is   */
+/* the one of the relaxation coefficients in Eq. D2Q9MOmega (the rates      */
+/* lambda_1 .. lambda_9 of the simulations): class 1 {0,5}<->{1,2}, 2       */
+/* {0,0}<->{1,3}, 3 {0,0}<->{5,7}, 4 {1,3}<->{5,7}, 5 {1,3}<->{2,4}, 6      */
+/* {5,7}<->{6,8}, 7 {0,1}<->{2,8}, 8 {1,6}<->{3,5}, 9 {1,1}<->{5,8}.        */
+/* Probabilities, as for D1Q3 (Sec. III.A): from the pair whose ordered     */
+/* picks are less likely at equilibrium (smaller m w_i w_j, m = 2 for two   */
+/* different velocities, 1 for equal ones) to the other pair lambda_c; back  */
+/* lambda_c times the ratio of the two m w w products (detailed balance).   */
+/* ======================================================================== */
+static const int V2X[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int V2Y[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+static int vel2(int vx, int vy)
+{
+    for (int i = 0; i < 9; i++)
+        if (V2X[i] == vx && V2Y[i] == vy) return i;
+    return -1;
+}
+
+/* m w_i w_j for the unordered pair {i, j}, in units of 1/1296 (w = 36/81,
+ * 9/81... written as 16/36^2 etc.): w_i * 36 is 16, 4 or 1. */
+static uint32_t mww(int i, int j)
+{
+    static const uint32_t w36[9] = {16, 4, 4, 4, 4, 1, 1, 1, 1};
+    return (i == j ? 1u : 2u) * w36[i] * w36[j];
+}
+
+typedef struct {
+    int a0, a1, b0, b1; /* the two unordered pairs (a0 <= a1, b0 <= b1) */
+    int cls;            /* 1 .. 9 */
+} coll2;
+
+static coll2 orc2_colls[64];
+static int orc2_ncolls = 0;
+
+static void orc2_add(int cls, int i, int j, int k, int l)
+{
+    int a0 = i < j ? i : j, a1 = i < j ? j : i, b0 = k < l ? k : l, b1 = k < l ? l : k;
+    if (a0 > b0 || (a0 == b0 && a1 > b1)) { /* store the smaller pair first */
+        int t0 = a0, t1 = a1;
+        a0 = b0; a1 = b1; b0 = t0; b1 = t1;
+    }
+    for (int c = 0; c < orc2_ncolls; c++)
+        if (orc2_colls[c].a0 == a0 && orc2_colls[c].a1 == a1 && orc2_colls[c].b0 == b0 &&
+            orc2_colls[c].b1 == b1)
+            return;
+    coll2 e = {a0, a1, b0, b1, cls};
+    orc2_colls[orc2_ncolls++] = e;
+}
+
+/* The 30 collisions: each class representative under the 8 symmetries
+ * (x, y) -> (sx * (swap ? y : x), sy * (swap ? x : y)). */
+static void orc2_build_collisions(void)
+{
+    if (orc2_ncolls) return;
+    static const int rep[9][4] = {{0, 5, 1, 2}, {0, 0, 1, 3}, {0, 0, 5, 7}, {1, 3, 5, 7},
+                                  {1, 3, 2, 4}, {5, 7, 6, 8}, {0, 1, 2, 8}, {1, 6, 3, 5},
+                                  {1, 1, 5, 8}};
+    for (int c = 0; c < 9; c++)
+        for (int sw = 0; sw < 2; sw++)
+            for (int sx = -1; sx <= 1; sx += 2)
+                for (int sy = -1; sy <= 1; sy += 2) {
+                    int img[4];
+                    for (int q = 0; q < 4; q++) {
+                        int x = V2X[rep[c][q]], y = V2Y[rep[c][q]];
+                        int nx = sx * (sw ? y : x), ny = sy * (sw ? x : y);
+                        img[q] = vel2(nx, ny);
+                    }
+                    orc2_add(c + 1, img[0], img[1], img[2], img[3]);
+                }
+}
+
+int orc2_collision_count(void)
+{
+    orc2_build_collisions();
+    return orc2_ncolls;
+}
+
+/* Collision k: its two pairs and class (for checking the table). */
+void orc2_collision(int k, int out[5])
+{
+    orc2_build_collisions();
+    out[0] = orc2_colls[k].a0; out[1] = orc2_colls[k].a1;
+    out[2] = orc2_colls[k].b0; out[3] = orc2_colls[k].b1;
+    out[4] = orc2_colls[k].cls;
+}
+
+/* Outcomes of an ordered pick of velocities (s1, s2) of two different
+ * particles: the pairs B it may turn into, in increasing order of (b0, b1),
+ * with integer numerators over D = 128 * lam_den: P = lam_num[c] / lam_den
+ * times the ratio mww(lower) / mww(upper) (a power of 2 down to 1/128) when
+ * the pick is the more likely pair.  Returns the number of outcomes. */
+int orc2_outcomes(int s1, int s2, const uint32_t lam_num[9], uint32_t lam_den, int targets[8],
+                  uint64_t nums[4])
+{
+    orc2_build_collisions();
+    int a0 = s1 < s2 ? s1 : s2, a1 = s1 < s2 ? s2 : s1;
+    int n = 0;
+    for (int c = 0; c < orc2_ncolls; c++) {
+        const coll2 *e = &orc2_colls[c];
+        int b0, b1;
+        if (e->a0 == a0 && e->a1 == a1) { b0 = e->b0; b1 = e->b1; }
+        else if (e->b0 == a0 && e->b1 == a1) { b0 = e->a0; b1 = e->a1; }
+        else continue;
+        uint32_t from = mww(a0, a1), to = mww(b0, b1);
+        /* lambda from the smaller m w w product; the other way scaled by the ratio */
+        uint64_t num = (uint64_t)lam_num[e->cls - 1] * 128u;
+        if (from > to) num = num * to / from; /* to / from = 2^-k with k <= 7: exact */
+        /* insert in increasing (b0, b1) */
+        int pos = n;
+        while (pos > 0 && (targets[2 * (pos - 1)] > b0 ||
+                           (targets[2 * (pos - 1)] == b0 && targets[2 * (pos - 1) + 1] > b1))) {
+            targets[2 * pos] = targets[2 * (pos - 1)];
+            targets[2 * pos + 1] = targets[2 * (pos - 1) + 1];
+            nums[pos] = nums[pos - 1];
+            pos--;
+        }
+        targets[2 * pos] = b0;
+        targets[2 * pos + 1] = b1;
+        nums[pos] = num;
+        n++;
+    }
+    (void)lam_den;
+    return n;
+}
+
+/* Entropic D2Q9 equilibrium, Eq. D2Q9eqdist: the product over x and y of the
+ * D1Q3 factors w_{v_a} [1 + 3 v_a u_a + (3 v_a^2 - 1)(sqrt(1 + 3 u_a^2) - 1)]. */
+void orc2_feq(double rho, double ux, double uy, double f[9])
+{
+    const double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0}; /* v = -1, 0, +1 */
+    double sx = sqrt(1.0 + 3.0 * ux * ux) - 1.0, sy = sqrt(1.0 + 3.0 * uy * uy) - 1.0;
+    for (int i = 0; i < 9; i++) {
+        double vx = V2X[i], vy = V2Y[i];
+        double gx = w1[V2X[i] + 1] * (1.0 + 3.0 * vx * ux + (3.0 * vx * vx - 1.0) * sx);
+        double gy = w1[V2Y[i] + 1] * (1.0 + 3.0 * vy * uy + (3.0 * vy * vy - 1.0) * sy);
+        f[i] = rho * gx * gy;
+    }
+}
+
+/* n_i(x, y, 0) ~ Poisson(f_i^eq(rho, ux, uy)) per node (Eq. poisson), split into
+ * parts of mean <= 32 like orc_init; part p of velocity i at node g = y Lx + x
+ * of replica r takes U from Philox block (g, r, p/2, PURPOSE_INIT << 28 | i),
+ * words (0, 1) for even p and (2, 3) for odd p.  n is [9][R Lx Ly]. */
+int orc2_init(uint32_t Lx, uint32_t Ly, uint32_t R, uint64_t seed, const double *rho,
+              const double *ux, const double *uy, uint16_t *n, uint32_t r0)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    const uint64_t G = (uint64_t)Lx * Ly, S = G * R;
+    int err = 0;
+    for (uint32_t r = 0; r < R; r++) {
+#pragma omp parallel for schedule(static) reduction(| : err)
+        for (uint64_t g = 0; g < G; g++) {
+            uint64_t o = (uint64_t)r * G + g;
+            double rh = rho[o], u1 = ux[o], u2 = uy[o];
+            if (!(rh >= 0.0) || !isfinite(rh) || !(fabs(u1) <= 1.0) || !(fabs(u2) <= 1.0)) {
+                err |= 8;
+                continue;
+            }
+            double f[9];
+            orc2_feq(rh, u1, u2, f);
+            for (uint32_t i = 0; i < 9; i++) {
+                double mu = f[i] > 0.0 ? f[i] : 0.0;
+                uint32_t parts = (uint32_t)ceil(mu / 32.0);
+                if (parts < 1) parts = 1;
+                double mup = mu / (double)parts;
+                uint64_t total = 0;
+                for (uint32_t p = 0; p < parts; p++) {
+                    uint32_t ctr[4] = {(uint32_t)g, r0 + r, p / 2, (PURPOSE_INIT << 28) | i}, w[4];
+                    orc_philox(ctr, key, w);
+                    uint32_t lo = (p % 2 == 0) ? w[0] : w[2];
+                    uint32_t hi = (p % 2 == 0) ? w[1] : w[3];
+                    uint64_t m = (((uint64_t)hi << 32) | lo) >> 11;
+                    total += orc_poisson_inv(mup, (double)m * (1.0 / 9007199254740992.0));
+                }
+                if (total > 65535) {
+                    err |= ORC_ERR_OVERFLOW;
+                    total = 65535;
+                }
+                n[i * S + o] = (uint16_t)total;
+            }
+        }
+    }
+    return (err & 8) ? 8 : err;
+}
+
+/* The stream of 32-bit random words of one node-step: word k is word k % 4 of
+ * Philox block (g, r, t, PURPOSE_D2Q9 << 28 | k / 4). */
+#define PURPOSE_D2Q9 5u
+#define D2Q9_MAX_WORDS 4096 /* per node-step: far beyond any use (a decision error past it) */
+
+typedef struct {
+    uint32_t g, r, t, k;
+    uint32_t w[4];
+    const uint32_t *key;
+} word2_stream;
+
+static int next_word2(word2_stream *s, uint32_t *out)
+{
+    if (s->k >= D2Q9_MAX_WORDS) return 0;
+    if (s->k % 4 == 0) {
+        uint32_t ctr[4] = {s->g, s->r, s->t, (PURPOSE_D2Q9 << 28) | (s->k / 4)};
+        orc_philox(ctr, s->key, s->w);
+    }
+    *out = s->w[s->k % 4];
+    s->k++;
+    return 1;
+}
+
+/* A uniform integer in [0, m), 1 <= m < 2^32, exactly: the multiply-shift
+ * method with rejection of Lemire (2019, "Fast random integer generation in an
+ * interval"): x m = hi 2^32 + lo with x a uniform word; lo < (2^32 - m) mod m
+ * is rejected and a new word drawn.  Returns 0 when the words run out. */
+static int uniform_below2(word2_stream *s, uint32_t m, uint32_t *out)
+{
+    uint32_t x;
+    if (!next_word2(s, &x)) return 0;
+    uint64_t prod = (uint64_t)x * m;
+    uint32_t lo = (uint32_t)prod;
+    if (lo < m) {
+        uint32_t thr = (uint32_t)(-m) % m; /* (2^32 - m) mod m */
+        while (lo < thr) {
+            if (!next_word2(s, &x)) return 0;
+            prod = (uint64_t)x * m;
+            lo = (uint32_t)prod;
+        }
+    }
+    *out = (uint32_t)(prod >> 32);
+    return 1;
+}
+
+/* The velocity of particle index q in [0, N): the smallest s with
+ * q < n_0 + ... + n_s (Eq. select, velocities in the numbering above). */
+static int velocity_of2(const uint32_t n[9], uint32_t q)
+{
+    uint32_t cum = 0;
+    for (int s = 0; s < 9; s++) {
+        cum += n[s];
+        if (q < cum) return s;
+    }
+    return 8;
+}
+
+/* C sub-collisions at one D2Q9 node (Sec. III's algorithm: two uniform
+ * particle picks; the same particle twice collides nothing; otherwise the
+ * pair's outcomes by one uniform integer below D = 128 lam_den against the
+ * cumulative numerators, none if it lies beyond them).  N < 2: nothing, no
+ * words. */
+static int collide2(uint32_t st[9], uint32_t g, uint32_t r, uint32_t t, uint32_t C,
+                    const uint32_t lam_num[9], uint32_t lam_den, const uint32_t key[2])
+{
+    uint32_t N = 0;
+    for (int i = 0; i < 9; i++) N += st[i];
+    if (N < 2) return 0;
+    word2_stream ws = {g, r, t, 0, {0, 0, 0, 0}, key};
+    const uint32_t D = 128u * lam_den;
+    for (uint32_t k = 0; k < C; k++) {
+        uint32_t q1, q2;
+        if (!uniform_below2(&ws, N, &q1) || !uniform_below2(&ws, N, &q2)) return ORC_ERR_SAMPLER;
+        if (q1 == q2) continue;
+        int s1 = velocity_of2(st, q1), s2 = velocity_of2(st, q2);
+        int targets[8];
+        uint64_t nums[4];
+        int no = orc2_outcomes(s1, s2, lam_num, lam_den, targets, nums);
+        if (no == 0) continue;
+        uint32_t u;
+        if (!uniform_below2(&ws, D, &u)) return ORC_ERR_SAMPLER;
+        uint64_t cum = 0;
+        for (int o = 0; o < no; o++) {
+            cum += nums[o];
+            if (u < cum) {
+                int b0 = targets[2 * o], b1 = targets[2 * o + 1];
+                st[s1]--; st[s2]--;
+                st[b0]++; st[b1]++;
+                if (st[b0] > 65535 || st[b1] > 65535) return ORC_ERR_OVERFLOW;
+                break;
+            }
+        }
+    }
+    return 0;
+}
+
+/* n_steps time steps of R periodic Lx x Ly lattices, n[9][R Lx Ly] with node
+ * g = y Lx + x of replica r at r Lx Ly + g; streaming n_i(x + v_i, t + 1) =
+ * post_i(x, t) (Sec. III's evolution equation in two dimensions). */
+int orc2_step(uint32_t Lx, uint32_t Ly, uint32_t R, uint64_t seed, uint32_t C,
+              const uint32_t lam_num[9], uint32_t lam_den, uint32_t flags, uint16_t *n,
+              uint64_t t0, uint64_t n_steps, uint32_t r0)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    orc2_build_collisions();
+    const uint64_t G = (uint64_t)Lx * Ly, S = G * R;
+    uint16_t *post = (uint16_t *)malloc(9 * S * sizeof(uint16_t) + 1);
+    if (!post) return 16;
+    int err = 0;
+    for (uint64_t s = 0; s < n_steps; s++) {
+        uint32_t t = (uint32_t)(t0 + s);
+        for (uint32_t r = 0; r < R; r++) {
+#pragma omp parallel for schedule(static) reduction(| : err)
+            for (uint64_t g = 0; g < G; g++) {
+                uint64_t o = (uint64_t)r * G + g;
+                uint32_t st[9];
+                for (int i = 0; i < 9; i++) st[i] = n[i * S + o];
+                err |= collide2(st, (uint32_t)g, r0 + r, t, C, lam_num, lam_den, key);
+                for (int i = 0; i < 9; i++) post[i * S + o] = (uint16_t)st[i];
+            }
+        }
+        if (flags & ORC_FLAG_NO_STREAM) {
+            memcpy(n, post, 9 * S * sizeof(uint16_t));
+            continue;
+        }
+        for (uint32_t r = 0; r < R; r++)
+            for (uint32_t y = 0; y < Ly; y++)
+                for (uint32_t x = 0; x < Lx; x++)
+                    for (int i = 0; i < 9; i++) {
+                        uint32_t xd = (x + Lx + V2X[i]) % Lx, yd = (y + Ly + V2Y[i]) % Ly;
+                        n[i * S + (uint64_t)r * G + (uint64_t)yd * Lx + xd] =
+                            post[i * S + (uint64_t)r * G + (uint64_t)y * Lx + x];
+                    }
+    }
+    free(post);
+    return err;
+}
+
+/* Density and momentum per node (Eq. MomD2Q9's first three moments without
+ * the sqrt(3) of the normalisation): rho = sum n_i, j = sum n_i v_i. */
+void orc2_moments(uint64_t S, const uint16_t *n, int32_t *rho, int32_t *jx, int32_t *jy,
+                  int64_t totals[3])
+{
+    totals[0] = totals[1] = totals[2] = 0;
+    for (uint64_t o = 0; o < S; o++) {
+        int32_t a = 0, bx = 0, by = 0;
+        for (int i = 0; i < 9; i++) {
+            int32_t v = n[i * S + o];
+            a += v;
+            bx += v * V2X[i];
+            by += v * V2Y[i];
+        }
+        rho[o] = a; jx[o] = bx; jy[o] = by;
+        totals[0] += a; totals[1] += bx; totals[2] += by;
     }
 }
