@@ -237,6 +237,86 @@ mclg_status mclg_halo_put(mclg_handle h, const uint16_t *in);
 /* Release every resource of the handle.  NULL-safe. */
 void mclg_destroy(mclg_handle h);
 
+/* ------------------------------------------------------------------------
+ * D2Q9 (Sec. II.B, III.B, IV.B): R periodic Lx x Ly lattices of the nine
+ * velocities v = (vx, vy), vx, vy in {-1, 0, 1}, numbered 0 = (0,0),
+ * 1 = (1,0), 2 = (0,1), 3 = (-1,0), 4 = (0,-1), 5 = (1,1), 6 = (-1,1),
+ * 7 = (-1,-1), 8 = (1,-1); state uint16 n[9][S], S = R Lx Ly, node
+ * g = y Lx + x of replica r at r Lx Ly + g.
+ *
+ * Sampling contract (identical on every path):
+ *   - Random words of node g of replica r at time t: word k of the node-step
+ *     is word k % 4 of Philox4x32-10 block (g, r, t, 5 << 28 | k / 4), key as
+ *     for D1Q3; at most 16 C + 64 words (MCLG_ERR_SAMPLER beyond).
+ *   - Uniform integer below m: Lemire's multiply-shift x m = hi 2^32 + lo of a
+ *     word x, rejecting lo < (2^32 - m) mod m with a new word; the value is hi.
+ *   - A node with N < 2 is left alone.  Each of the C sub-collisions (Sec. III):
+ *     q1, q2 uniform below N; q1 == q2: nothing; else s = the smallest
+ *     velocity with q < n_0 + ... + n_s for each pick; the pick (s1, s2) has
+ *     the outcome list of mclg2d_pair_outcomes (target pairs in increasing
+ *     order, numerators over D = 128 lambda_den); then u uniform below D picks
+ *     the first outcome whose cumulative numerator exceeds u, or nothing.
+ *   - Collision classes (Sec. III.B, numbered as the rates in Eq. D2Q9MOmega):
+ *     1 {0,5}<->{1,2}, 2 {0,0}<->{1,3}, 3 {0,0}<->{5,7}, 4 {1,3}<->{5,7},
+ *     5 {1,3}<->{2,4}, 6 {5,7}<->{6,8}, 7 {0,1}<->{2,8}, 8 {1,6}<->{3,5},
+ *     9 {1,1}<->{5,8}, each with its images under the rotations and
+ *     reflections of the square.  From the pair with the smaller equilibrium
+ *     pick weight (2 w_i w_j for different velocities, w_i^2 for equal ones) to
+ *     the other: lambda_c; the other way: lambda_c times the ratio of the two
+ *     weights (detailed balance; a power of 2 down to 1/128).
+ *   - Streaming: n_i(x + v_i, t + 1) = post-collision n_i(x, t), periodic.
+ *   - mclg2d_init: n_i ~ Poisson(f_i^eq(rho, u)) of Eq. D2Q9eqdist, by the
+ *     D1Q3 initialisation contract with counters (g, r, p/2, 2 << 28 | i).
+ * ------------------------------------------------------------------------ */
+typedef struct mclg2d_ctx *mclg2d_handle;
+
+typedef struct {
+    uint32_t C;               /* sub-collisions per node and step (<= 2^24) */
+    uint32_t lambda_num[9];   /* class rates lambda_c = lambda_num[c-1] / lambda_den */
+    uint32_t lambda_den;      /* 1 .. 65536; every pick's outcomes must add up to <= 1 */
+    uint32_t flags;           /* MCLG_NO_STREAM */
+    uint32_t first_replica;   /* random-stream index of replica 0 */
+} mclg2d_params;
+
+/* Defaults: C = 10 and the rates of the paper's D2Q9 runs (Sec. IV.B):
+ * lambda_1 = 15/128, lambda_2..7 = 1/4, lambda_8 = 1/8, lambda_9 = 18/144. */
+void mclg2d_default_params(mclg2d_params *p);
+
+/* R replicas of an Lx x Ly periodic lattice (Lx Ly < 2^32); p = NULL: defaults.
+ * MCLG_ERR_ARG for invalid sizes or rates (including outcome probabilities of a
+ * pick that add up to more than 1). */
+mclg_status mclg2d_create(uint32_t Lx, uint32_t Ly, uint32_t replicas, uint64_t seed,
+                          const mclg2d_params *p, void *cuda_stream, mclg2d_handle *out);
+
+/* n_i ~ Poisson(f_i^eq(rho, ux, uy)) (Eq. D2Q9eqdist, Eq. poisson); host arrays
+ * of S doubles (rho >= 0, |u| <= 1).  Sets t = 0. */
+mclg_status mclg2d_init(mclg2d_handle h, const double *rho, const double *ux, const double *uy);
+
+/* Replace / read the state n[9][S] (host or device) at time t (< 2^32); reading
+ * synchronises and returns the sticky device error, if any. */
+mclg_status mclg2d_set_state(mclg2d_handle h, const uint16_t *n, uint64_t t);
+mclg_status mclg2d_get_state(mclg2d_handle h, uint16_t *n, uint64_t *t);
+
+/* Advance n_steps time steps (asynchronous). */
+mclg_status mclg2d_step(mclg2d_handle h, uint64_t n_steps);
+
+/* Density and momentum per node (device int32 arrays of S entries, or NULL)
+ * and the exact totals (sum rho, sum j_x, sum j_y) into totals[3] (host, or
+ * NULL).  Synchronises. */
+mclg_status mclg2d_moments(mclg2d_handle h, int32_t *rho, int32_t *jx, int32_t *jy,
+                           int64_t *totals);
+
+mclg_status mclg2d_sync(mclg2d_handle h);
+uint64_t mclg2d_time(mclg2d_handle h);
+void mclg2d_destroy(mclg2d_handle h);
+
+/* The outcome list of a pick of velocities (s1, s2) under the rates of p (host
+ * computation, no GPU): *count outcomes, target pairs targets[2k], targets[2k+1]
+ * (increasing), numerators nums[k] over 128 lambda_den (arrays of 4 entries,
+ * targets of 8; either may be NULL).  For checking the table independently. */
+mclg_status mclg2d_pair_outcomes(uint32_t s1, uint32_t s2, const mclg2d_params *p,
+                                 uint32_t *count, uint32_t *targets, uint64_t *nums);
+
 /* Static description of a status code. */
 const char *mclg_status_str(mclg_status s);
 

@@ -1211,17 +1211,18 @@ int orc2_init(uint32_t Lx, uint32_t Ly, uint32_t R, uint64_t seed, const double 
 /* The stream of 32-bit random words of one node-step: word k is word k % 4 of
  * Philox block (g, r, t, PURPOSE_D2Q9 << 28 | k / 4). */
 #define PURPOSE_D2Q9 5u
-#define D2Q9_MAX_WORDS 4096 /* per node-step: far beyond any use (a decision error past it) */
 
+/* Words of a node-step: at most 16 C + 64 (a sub-collision takes 2 or 3 plus
+ * the rare rejections; running out is reported as a sampler error). */
 typedef struct {
-    uint32_t g, r, t, k;
+    uint32_t g, r, t, k, cap;
     uint32_t w[4];
     const uint32_t *key;
 } word2_stream;
 
 static int next_word2(word2_stream *s, uint32_t *out)
 {
-    if (s->k >= D2Q9_MAX_WORDS) return 0;
+    if (s->k >= s->cap) return 0;
     if (s->k % 4 == 0) {
         uint32_t ctr[4] = {s->g, s->r, s->t, (PURPOSE_D2Q9 << 28) | (s->k / 4)};
         orc_philox(ctr, s->key, s->w);
@@ -1276,7 +1277,7 @@ static int collide2(uint32_t st[9], uint32_t g, uint32_t r, uint32_t t, uint32_t
     uint32_t N = 0;
     for (int i = 0; i < 9; i++) N += st[i];
     if (N < 2) return 0;
-    word2_stream ws = {g, r, t, 0, {0, 0, 0, 0}, key};
+    word2_stream ws = {g, r, t, 0, 16u * C + 64u, {0, 0, 0, 0}, key};
     const uint32_t D = 128u * lam_den;
     for (uint32_t k = 0; k < C; k++) {
         uint32_t q1, q2;

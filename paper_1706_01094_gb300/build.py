@@ -1,7 +1,8 @@
 """Build the sm_103a library ``_build/libmclg.so`` in-tree with nvcc.
 
-Two translation units (kernels, host ABI) compile in parallel, then link into
-one shared library with the CUDA runtime linked statically.  Host code is
+The translation units (kernels, host ABI, slice tables and kernels, the
+allocation-free moments, D2Q9) compile in parallel, then link into one shared
+library with the CUDA runtime linked statically.  Host code is
 compiled without floating-point contraction so the FP64 initialisation is
 reproducible.
 """
@@ -18,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmclg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["mclg_kernels.cu", "mclg_api.cu", "mclg_noalloc.cu", "mclg_slice_table.cu",
-           "mclg_slice_kernel.cu"]
+           "mclg_slice_kernel.cu", "mclg_d2q9.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

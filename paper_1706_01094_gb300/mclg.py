@@ -30,7 +30,9 @@ EXPORTS = ["mclg_default_params", "mclg_create", "mclg_init", "mclg_set_state",
            "mclg_get_state", "mclg_step", "mclg_moments", "mclg_stats_reset", "mclg_stats_read",
            "mclg_sync", "mclg_time", "mclg_destroy", "mclg_status_str", "mclg_philox",
            "mclg_moments_noalloc", "mclg_tuning", "mclg_slice_row", "mclg_halo_get",
-           "mclg_halo_put"]
+           "mclg_halo_put", "mclg2d_default_params", "mclg2d_create", "mclg2d_init",
+           "mclg2d_set_state", "mclg2d_get_state", "mclg2d_step", "mclg2d_moments",
+           "mclg2d_sync", "mclg2d_time", "mclg2d_destroy", "mclg2d_pair_outcomes"]
 
 
 class MCLGError(RuntimeError):
@@ -45,6 +47,12 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_uint32), ("first_replica", ctypes.c_uint32),
                 ("sampler", ctypes.c_uint32), ("slice_n_max", ctypes.c_uint32),
                 ("kernel_variant", ctypes.c_uint32), ("node_offset", ctypes.c_uint32)]
+
+
+class Params2D(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_uint32), ("lambda_num", ctypes.c_uint32 * 9),
+                ("lambda_den", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("first_replica", ctypes.c_uint32)]
 
 
 _lib = None
@@ -105,6 +113,28 @@ def load() -> ctypes.CDLL:
         lib.mclg_halo_get.restype = st
         lib.mclg_halo_put.argtypes = [P, P]
         lib.mclg_halo_put.restype = st
+        lib.mclg2d_default_params.argtypes = [ctypes.POINTER(Params2D)]
+        lib.mclg2d_create.argtypes = [u32, u32, u32, u64, ctypes.POINTER(Params2D), P,
+                                      ctypes.POINTER(P)]
+        lib.mclg2d_create.restype = st
+        lib.mclg2d_init.argtypes = [P, P, P, P]
+        lib.mclg2d_init.restype = st
+        lib.mclg2d_set_state.argtypes = [P, P, u64]
+        lib.mclg2d_set_state.restype = st
+        lib.mclg2d_get_state.argtypes = [P, P, ctypes.POINTER(u64)]
+        lib.mclg2d_get_state.restype = st
+        lib.mclg2d_step.argtypes = [P, u64]
+        lib.mclg2d_step.restype = st
+        lib.mclg2d_moments.argtypes = [P, P, P, P, P]
+        lib.mclg2d_moments.restype = st
+        lib.mclg2d_sync.argtypes = [P]
+        lib.mclg2d_sync.restype = st
+        lib.mclg2d_time.argtypes = [P]
+        lib.mclg2d_time.restype = u64
+        lib.mclg2d_destroy.argtypes = [P]
+        lib.mclg2d_destroy.restype = None
+        lib.mclg2d_pair_outcomes.argtypes = [u32, u32, ctypes.POINTER(Params2D), P, P, P]
+        lib.mclg2d_pair_outcomes.restype = st
         _lib = lib
         return lib
 
@@ -330,3 +360,102 @@ def philox(ctr, seed: int, out=None, stream=None):
     _check(lib.mclg_philox(_ptr(ctr), n, seed & (2**64 - 1), _ptr(out), _stream_ptr(stream)),
            "mclg_philox")
     return out
+
+
+# ---------------------------------------------------------------------- D2Q9 ---
+D2Q9_PAPER_LAMBDA = ((15, 32, 32, 32, 32, 32, 32, 16, 16), 128)  # Sec. IV.B's rates
+
+
+def params2d(C: int = 10, lam=D2Q9_PAPER_LAMBDA, flags: int = 0, first_replica: int = 0):
+    p = Params2D()
+    p.C = C
+    for k in range(9):
+        p.lambda_num[k] = int(lam[0][k])
+    p.lambda_den = int(lam[1])
+    p.flags = flags
+    p.first_replica = first_replica
+    return p
+
+
+def pair_outcomes2d(s1: int, s2: int, lam=D2Q9_PAPER_LAMBDA):
+    """The library's outcome list of a pick of velocities (s1, s2): [(target pair,
+    numerator over 128 lambda_den)] (host computation)."""
+    lib = load()
+    p = params2d(lam=lam)
+    cnt = ctypes.c_uint32(0)
+    tg = np.zeros(8, dtype=np.uint32)
+    nums = np.zeros(4, dtype=np.uint64)
+    _check(lib.mclg2d_pair_outcomes(s1, s2, ctypes.byref(p), ctypes.byref(cnt), _ptr(tg), _ptr(nums)),
+           "mclg2d_pair_outcomes")
+    return [((int(tg[2 * k]), int(tg[2 * k + 1])), int(nums[k])) for k in range(cnt.value)]
+
+
+class Lattice2D:
+    """A D2Q9 handle: `replicas` periodic Lx x Ly lattices (state n[9, R Lx Ly])."""
+
+    def __init__(self, Lx: int, Ly: int, replicas: int = 1, seed: int = 1, C: int = 10,
+                 lam=D2Q9_PAPER_LAMBDA, flags: int = 0, stream=None, first_replica: int = 0):
+        self._lib = load()
+        self.Lx, self.Ly, self.R = int(Lx), int(Ly), int(replicas)
+        self.S = self.Lx * self.Ly * self.R
+        p = params2d(C, lam, flags, first_replica)
+        h = ctypes.c_void_p()
+        _check(self._lib.mclg2d_create(self.Lx, self.Ly, self.R, int(seed) & (2**64 - 1),
+                                       ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)),
+               "mclg2d_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mclg2d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, rho, ux, uy):
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)) for a in (rho, ux, uy)]
+        if any(a.size != self.S for a in arrs):
+            raise ValueError("rho, ux, uy need one value per node")
+        _check(self._lib.mclg2d_init(self._h, *[_ptr(a) for a in arrs]), "mclg2d_init")
+
+    def set_state(self, n, t: int = 0):
+        if isinstance(n, np.ndarray):
+            n = np.ascontiguousarray(n, dtype=np.uint16)
+        if tuple(n.shape) not in ((9, self.S), (9 * self.S,)):
+            raise ValueError("state must be [9, S]")
+        _check(self._lib.mclg2d_set_state(self._h, _ptr(n), t), "mclg2d_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((9, self.S), dtype=np.uint16)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.mclg2d_get_state(self._h, _ptr(out), ctypes.byref(t)), "mclg2d_get_state")
+        return out, int(t.value)
+
+    def step(self, n_steps: int = 1):
+        _check(self._lib.mclg2d_step(self._h, n_steps), "mclg2d_step")
+
+    def sync(self):
+        _check(self._lib.mclg2d_sync(self._h), "mclg2d_sync")
+
+    @property
+    def t(self) -> int:
+        return int(self._lib.mclg2d_time(self._h))
+
+    def moments(self, rho=None, jx=None, jy=None):
+        """Per-node density and momentum into device int32 tensors (or None) and the
+        exact totals (host)."""
+        tot = np.zeros(3, dtype=np.int64)
+        _check(self._lib.mclg2d_moments(self._h, _ptr(rho), _ptr(jx), _ptr(jy), _ptr(tot)),
+               "mclg2d_moments")
+        return tot

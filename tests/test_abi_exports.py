@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "mclg.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mclg_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mclg(?:2d)?_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(libpath):
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True)
     if out.returncode == 0:
-        exported = set(re.findall(r"\bT (mclg_[a-z0-9_]+)", out.stdout))
+        exported = set(re.findall(r"\bT (mclg(?:2d)?_[a-z0-9_]+)", out.stdout))
         assert set(declared_functions()) <= exported
 
 

@@ -25,6 +25,9 @@ int main(void) {
            MCLG_MODE_AUTO, MCLG_MODE_PLAIN, MCLG_MODE_PERSISTENT, MCLG_MODE_BATCHED);
     printf("SAMPLER_SEQUENTIAL %u\nSAMPLER_SLICE %u\n", MCLG_SAMPLER_SEQUENTIAL, MCLG_SAMPLER_SLICE);
     printf("status_max %d\n", (int)MCLG_ERR_SAMPLER);
+    printf("size2d %zu\n", sizeof(mclg2d_params));
+#define F2(name) printf("off2d_" #name " %zu\n", offsetof(mclg2d_params, name));
+    F2(C) F2(lambda_num) F2(lambda_den) F2(flags) F2(first_replica)
     return 0;
 }
 """
@@ -55,6 +58,9 @@ def test_params_struct_layout_matches_header(header_values):
     for name, _ in m.Params._fields_:
         assert getattr(m.Params, name).offset == header_values["off_" + name], name
     assert {n for n, _ in m.Params._fields_} == {k[4:] for k in header_values if k.startswith("off_")}
+    assert ctypes.sizeof(m.Params2D) == header_values["size2d"]
+    for name, _ in m.Params2D._fields_:
+        assert getattr(m.Params2D, name).offset == header_values["off2d_" + name], name
 
 
 def test_constants_match_header(header_values):

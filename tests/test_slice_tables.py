@@ -95,3 +95,18 @@ def test_rows_at_the_largest_accepted_denominators_equal_oracle(lib):
         assert 8 * N * N * ld >= 2**44
         with pytest.raises(lib.MCLGError):
             lib.slice_row(N, 0, N % 2, 10, (1, ld))
+
+
+def test_d2q9_outcome_table_equals_oracle(lib):
+    """The library's D2Q9 outcome table (built on the host from its own class
+    list) against the oracle's, for every ordered pick and three rate sets,
+    and a rate set whose probabilities exceed 1 is refused."""
+    import oracle
+    for lam in (oracle.D2Q9_PAPER_LAMBDA, ((128, 64, 32, 16, 8, 4, 2, 1, 96), 128),
+                ((1, 2, 3, 4, 5, 6, 7, 8, 9), 37)):
+        for s1 in range(9):
+            for s2 in range(9):
+                assert lib.pair_outcomes2d(s1, s2, lam) == oracle.d2q9_outcomes(s1, s2, lam), \
+                    (s1, s2, lam)
+    with pytest.raises(lib.MCLGError):   # from {5,7}: lambda_3 + 2 lambda_4 + lambda_6 > 1
+        lib.pair_outcomes2d(5, 7, ((1, 1, 64, 64, 1, 64, 1, 1, 1), 128))
