@@ -81,7 +81,9 @@ typedef enum {
                              node node_offset + x for every random number, and its two edges
                              exchange one value each per step with the neighbouring blocks
                              (mclg_halo_get / mclg_halo_put).  One replica, no MCLG_STATS, not
-                             MCLG_MODE_PERSISTENT; with the SLICE sampler node_offset is even. */
+                             MCLG_MODE_PERSISTENT; with the SLICE sampler node_offset is a
+                             multiple of 8 (eight consecutive nodes share the Philox block of
+                             their uniforms' top bits). */
 
 /* samplers: two exact ways to draw the C sub-collisions of a node, with
  * different uses of the random bits (each is bit-exact to its own oracle):
@@ -90,8 +92,10 @@ typedef enum {
  *   SLICE       all C at once: the rest count b moves to b + 2d with the exact
  *               C-step law on the node's (N, J) slice (the C-th power of the
  *               one-sub-collision matrix), inverted with one 64-bit uniform
- *               prefix Q = w1 2^32 + w0, words (0, 1) of Philox block
- *               (x/2, r, t, 4 << 28) for even x, words (2, 3) for odd x;
+ *               prefix Q = h 2^48 + (w1 mod 2^16) 2^32 + w0: h is bits
+ *               [16 (x mod 2), 16 (x mod 2) + 16) of word (x/2) mod 4 of
+ *               Philox block (x/8, r, t, 6 << 28), (w0, w1) words (0, 1) of
+ *               block (x/2, r, t, 4 << 28) for even x, words (2, 3) for odd x;
  *               d = dmin + #{d' in [dmin, dmax) : Q > F[d']} with
  *               F[d'] = min(floor(CDF[d'] 2^64), 2^64 - 1) over the reachable
  *               offsets, Q == F[d'] reported as MCLG_ERR_SAMPLER.  Tables of F
@@ -124,15 +128,18 @@ typedef struct {
                                with a larger mass takes the SEQUENTIAL sampler's C
                                decisions (the same bits that sampler gives it).  The bits
                                depend on slice_n_max like on the seed.  Tables take about
-                               1184 (n+1)^3 / 12 bytes of device memory and as much host
-                               memory while they are built (1.7 GB at 256, 13.4 GB at 512,
-                               107 GB at 1024, where the 32-bit row index still holds);
-                               built once, at the first mclg_step, on the host cores. */
+                               21 n^3 bytes of device memory and as much host memory
+                               while they are built (0.37 GB at 256, 2.9 GB at 512,
+                               23 GB at 1024, where the 32-bit record index still
+                               holds); built once, at the first mclg_step, on the host
+                               cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
                                 mclg_step; v + 1 = use variant v (SEQUENTIAL: 0 <= v < 6, nodes
-                                per thread and register bound; SLICE: 0 <= v < 10, 0-5 likewise,
-                                6-9 the warp-specialised form with bulk-copy staging, which
-                                applies to single-replica launches; reported by mclg_tuning).
+                                per thread and register bound; SLICE: 0 <= v < 14, 0-5 likewise,
+                                6-9 the warp-specialised form with bulk-copy staging, 10-13 a
+                                grid-stride form that loads each warp's next tile while it
+                                draws the current one; 6-13 apply to single-replica launches;
+                                reported by mclg_tuning).
                                 Every variant gives the same bits; this only fixes the launch
                                 shape. */
     uint32_t node_offset;    /* MCLG_HALO: index of the block's first node in the whole lattice
@@ -347,18 +354,19 @@ mclg_status mclg_moments_noalloc(const uint16_t *n, uint64_t S, int32_t *N, int3
 /* The slice sampler's table row for the state (N, J, b) (host computation, no
  * GPU): F[k] = min(floor(CDF[dmin + k] 2^64), 2^64 - 1) for k < dmax - dmin,
  * the exact cumulative C-step law of the rest count (F holds 2C entries);
- * *dmin, *dmax the reachable offsets.  guide (512 uint16, or NULL) receives
- * the row's guide entries as the device reads them; for bucket j =
- * [j 2^55, (j+1) 2^55): bits 0-4 #{k : F[k] < j 2^55}, bits 5-6
- * min(#{k : F[k] in bucket j}, 3), bits 8-15 bits 54..47 of that F[k] when
- * it is the only one in the bucket (else 0).
+ * *dmin, *dmax the reachable offsets.  record (8 uint16, or NULL) receives
+ * the state's record as the device reads it: lane j = F[c0 - 4 + j] >> 49
+ * with c0 = -dmin (0 where c0 - 4 + j < 0, 0x7FFF where it is >= dmax -
+ * dmin).  If q = Q >> 49 equals no lane and lies above lane 0 and below lane
+ * 7, the draw is d = #{lanes below q} - 4; otherwise the kernel compares Q
+ * with the u64 values.
  * For checking the tables against an independent computation.  MCLG_ERR_ARG
  * for C > 10, an invalid state, or D = 8 N^2 lambda_den >= 2^44 (the exact
  * numerators over D^C would not fit the builder's 512-bit integers; with
  * lambda_den = 1 every N <= 2^20 is accepted, with 256 every N <= 92681). */
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
-                           uint16_t *guide);
+                           uint16_t *record);
 
 /* Philox4x32-10 of the library's device generator on n counters: ctr and out
  * are device arrays of n uint4 (x, y, z, w); key = (seed lo, seed hi).  For

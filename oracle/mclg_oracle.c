@@ -614,9 +614,12 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
 /* integers.  The node then takes b' = b + 2 d with d the first offset whose */
 /* cumulative probability CDF[d] exceeds a uniform U.                        */
 /*                                                                          */
-/* Contract: U's first 64 bits are Q = w1 2^32 + w0 with (w0, w1) = words    */
-/* (0, 1) of Philox block (x/2, r, t, PURPOSE_SLICE << 28) for even x and    */
-/* words (2, 3) for odd x; F[d] = min(floor(CDF[d] 2^64), 2^64 - 1); for d in */
+/* Contract: U's first 64 bits are Q = h 2^48 + (w1 mod 2^16) 2^32 + w0:    */
+/* h, the top 16 bits, is bits [16 (x mod 2), 16 (x mod 2) + 16) of word     */
+/* (x/2) mod 4 of Philox block (x/8, r, t, PURPOSE_SLICE_TOP << 28), so      */
+/* eight consecutive nodes share one block; (w0, w1) are words (0, 1) of     */
+/* block (x/2, r, t, PURPOSE_SLICE << 28) for even x and words (2, 3) for    */
+/* odd x; F[d] = min(floor(CDF[d] 2^64), 2^64 - 1); for d in                 */
 /* [dmin, dmax) (the reachable range, CDF[dmax] = 1) U >= CDF[d] when         */
 /* Q > F[d], U < CDF[d] when Q < F[d]; Q == F[d] is reported as              */
 /* ORC_ERR_SAMPLER (probability below 2^-59 per node-step).  C <= 10.        */
@@ -628,6 +631,7 @@ double orc_exact_cov(int64_t sij, int64_t si, int64_t sj, uint64_t M)
 /* depend on n_max as they depend on the seed.                              */
 /* ------------------------------------------------------------------------ */
 #define PURPOSE_SLICE 4u
+#define PURPOSE_SLICE_TOP 6u
 #define SLICE_MAX_C 10
 #define BN_LIMBS 20 /* 640-bit unsigned integers in 32-bit limbs */
 
@@ -858,11 +862,14 @@ int orc_slice_cdf(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lam_n,
  * contract above). */
 uint64_t orc_slice_q(uint32_t x, uint32_t r, uint32_t t, const uint32_t key[2])
 {
+    uint32_t top_ctr[4] = {x / 8, r, t, PURPOSE_SLICE_TOP << 28}, top[4];
+    orc_philox(top_ctr, key, top);
+    uint64_t h = (top[(x / 2) % 4] >> (16 * (x % 2))) & 0xFFFFu;
     uint32_t ctr[4] = {x / 2, r, t, PURPOSE_SLICE << 28}, w[4];
     orc_philox(ctr, key, w);
     uint32_t lo = (x % 2 == 0) ? w[0] : w[2];
-    uint32_t hi = (x % 2 == 0) ? w[1] : w[3];
-    return ((uint64_t)hi << 32) | lo;
+    uint32_t mid = ((x % 2 == 0) ? w[1] : w[3]) & 0xFFFFu;
+    return (h << 48) | ((uint64_t)mid << 32) | lo;
 }
 
 /* The new rest count of one node, or -1 for an undecided prefix. */

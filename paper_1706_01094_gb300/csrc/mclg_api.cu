@@ -67,7 +67,7 @@ struct mclg_ctx {
     uint32_t *d_rowstart = nullptr;
     unsigned long long *d_heavy_pos = nullptr;  // slice sampler: nodes beyond the tables
     uint32_t *d_heavy_ctl = nullptr;
-    uint16_t *d_slice_guide = nullptr;
+    uint4 *d_slice_record = nullptr;
     unsigned long long *d_slice_secondary = nullptr;
     uint64_t stats_count = 0;
     // a block of a larger lattice (MCLG_HALO): the two arriving edge values
@@ -179,10 +179,23 @@ PlainArgs plain_args(const mclg_ctx *h, const uint16_t *in, uint16_t *out, uint6
 
 bool streaming(const mclg_ctx *h) { return !(h->prm.flags & MCLG_NO_STREAM); }
 
-// One step over internal replicas [k_begin, k_end) with a single plain launch.
+// Steps that one launch of the plain path over [kb, ke) covers: the
+// temporally blocked slice variants advance a handle's single replica several
+// steps per launch; everything else one (the persistent mode's long replicas
+// must end in the buffer that the step count's parity gives).
+uint32_t launch_span(const mclg_ctx *h, uint32_t kb, uint32_t ke)
+{
+    if (h->prm.sampler != MCLG_SAMPLER_SLICE || kb != 0u || ke != 1u || h->R != 1u || h->halo ||
+        (h->prm.flags & MCLG_STATS) || h->plain_variant < kSliceTbFirst)
+        return 1u;
+    return slice_tb_steps(h->plain_variant - kSliceTbFirst);
+}
+
+// `steps` steps (1, or up to launch_span) over internal replicas
+// [k_begin, k_end) with a single plain launch.
 cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uint64_t t,
                              uint32_t k_begin, uint32_t k_end, cudaStream_t s,
-                             const uint32_t *t_dev = nullptr)
+                             const uint32_t *t_dev = nullptr, uint32_t steps = 1)
 {
     if (k_begin >= k_end) return cudaSuccess;
     PlainArgs a = plain_args(h, in, out, t);
@@ -194,6 +207,10 @@ cudaError_t plain_batch_step(mclg_ctx *h, const uint16_t *in, uint16_t *out, uin
         a.one_off = h->rep_off[k_begin];
         a.one_L = h->rep_L[k_begin];
         a.one_rid = h->order[k_begin];
+    }
+    if (steps > 1u) {
+        if (steps > launch_span(h, k_begin, k_end)) return cudaErrorInvalidValue;
+        return launch_slice_tb(a, h->slice, steps, h->plain_variant - kSliceTbFirst, s);
     }
     if (h->prm.sampler == MCLG_SAMPLER_SLICE) return launch_slice(a, one, h->slice, s);
     return launch_plain(a, one, s);
@@ -314,7 +331,7 @@ mclg_status autotune(mclg_ctx *h)
 
 bool fused_stats(const mclg_ctx *h);
 cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t ke,
-                           cudaStream_t s, const uint32_t *t_dev);
+                           cudaStream_t s, const uint32_t *t_dev, uint32_t steps = 1);
 
 // Plain-kernel autotuner: time each vector width on the real input, writing
 // into the buffer the next step overwrites anyway (results do not depend on
@@ -362,18 +379,22 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
         h->prm.sampler == MCLG_SAMPLER_SLICE ? kSliceVariants : kPlainVariants;
     for (uint32_t v = 0; v < variants; ++v) {
         h->plain_variant = v;
+        // per step: a blocked variant is timed over the steps one launch covers
+        const bool per_replica = mode == MCLG_MODE_PLAIN && h->R > 1u;
+        const uint32_t span = per_replica ? 1u : launch_span(h, k_begin, k_end);
         float ms = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {  // first launch warms up, keep the best of 3
             MCLG_CK(cudaEventRecord(e0, h->stream));
-            if (mode == MCLG_MODE_PLAIN)
+            if (per_replica)
                 MCLG_CK(plain_per_replica_step(h, in, outb, h->t, h->stream));
             else
-                MCLG_CK(plain_batch_step(h, in, outb, h->t, k_begin, k_end, h->stream));
+                MCLG_CK(plain_batch_step(h, in, outb, h->t, k_begin, k_end, h->stream, nullptr,
+                                         span));
             MCLG_CK(cudaEventRecord(e1, h->stream));
             MCLG_CK(cudaEventSynchronize(e1));
             float one = 0;
             MCLG_CK(cudaEventElapsedTime(&one, e0, e1));
-            if (rep > 0) ms = std::min(ms, one);
+            if (rep > 0) ms = std::min(ms, one / float(span));
         }
         if (ms < best) {
             best = ms;
@@ -401,13 +422,14 @@ cudaError_t stats_partial(mclg_ctx *h, int c, cudaStream_t s)
                                 streaming(h) ? 1 : 0, h->d_stat_partials, h->st.count + 2, s);
 }
 
-// One step of the plain path over internal replicas [kb, ke) from buffer c,
-// plus the statistics when they are on: of the new field (partial pass after
-// the step), or, in the slice sampler's statistics form, of the input field
-// inside the step kernel.  With t_dev set the launches read their time step
-// from the device (t is then an offset).
+// One launch of the plain path over internal replicas [kb, ke) from buffer c
+// to buffer c ^ 1 (`steps` steps, at most launch_span), plus the statistics
+// when they are on: of the new field (partial pass after the step), or, in
+// the slice sampler's statistics form, of the input field inside the step
+// kernel.  With t_dev set the launches read their time step from the device
+// (t is then an offset).
 cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t ke,
-                           cudaStream_t s, const uint32_t *t_dev)
+                           cudaStream_t s, const uint32_t *t_dev, uint32_t steps)
 {
     if (fused_stats(h)) {
         PlainArgs a = plain_args(h, h->d_B[c], h->d_B[c ^ 1], t);
@@ -419,7 +441,7 @@ cudaError_t plain_step_seq(mclg_ctx *h, int c, uint64_t t, uint32_t kb, uint32_t
                      h->stats_config};
         return launch_slice_stats(a, h->slice, sa, s);
     }
-    cudaError_t e = plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], t, kb, ke, s, t_dev);
+    cudaError_t e = plain_batch_step(h, h->d_B[c], h->d_B[c ^ 1], t, kb, ke, s, t_dev, steps);
     if (e != cudaSuccess) return e;
     if (h->prm.flags & MCLG_STATS) e = stats_partial(h, c ^ 1, s);
     return e;
@@ -454,8 +476,10 @@ mclg_status capture_graph(mclg_ctx *h, int c, uint32_t kb, uint32_t ke)
     MCLG_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     int cc = c;
-    for (uint32_t j = 0; j < kGraphSteps && e == cudaSuccess; ++j) {
-        e = plain_step_seq(h, cc, j, kb, ke, h->cap, h->d_t);
+    // an even number of launches (each flips the buffer): spans divide kGraphSteps / 2
+    const uint32_t span = launch_span(h, kb, ke);
+    for (uint32_t j = 0; j < kGraphSteps && e == cudaSuccess; j += span) {
+        e = plain_step_seq(h, cc, j, kb, ke, h->cap, h->d_t, span);
         cc ^= 1;
     }
     if (e == cudaSuccess) e = stats_merge(h, h->cap);  // one merge per graph
@@ -490,9 +514,12 @@ mclg_status plain_steps(mclg_ctx *h, int c, uint64_t t, uint64_t n_steps, uint32
         for (uint64_t g = 0; g < groups; ++g) MCLG_CK(cudaGraphLaunch(h->graph[c], s));
         done = groups * kGraphSteps;  // even: the parity of c is unchanged
     }
-    for (; done < n_steps; ++done) {
-        MCLG_CK(plain_step_seq(h, c, t + done, kb, ke, s, nullptr));
+    const uint32_t span = launch_span(h, kb, ke);
+    while (done < n_steps) {
+        const uint32_t k = uint32_t(std::min<uint64_t>(span, n_steps - done));
+        MCLG_CK(plain_step_seq(h, c, t + done, kb, ke, s, nullptr, k));
         c ^= 1;
+        done += k;
     }
     if (fused_stats(h)) MCLG_CK(stats_partial(h, c, s));  // the call's last field
     MCLG_CK(stats_merge(h, s));  // every call leaves the statistics merged
@@ -507,10 +534,10 @@ void free_slice_tables(mclg_ctx *h)
     cudaFree(h->d_heavy_ctl);
     h->d_heavy_pos = nullptr;
     h->d_heavy_ctl = nullptr;
-    cudaFree(h->d_slice_guide);
+    cudaFree(h->d_slice_record);
     cudaFree(h->d_slice_secondary);
     h->d_rowstart = nullptr;
-    h->d_slice_guide = nullptr;
+    h->d_slice_record = nullptr;
     h->d_slice_secondary = nullptr;
     h->slice = SliceTables{};
 }
@@ -520,14 +547,14 @@ void free_slice_tables(mclg_ctx *h)
 // sequential draws in a second pass of each step.
 mclg_status ensure_slice_tables(mclg_ctx *h)
 {
-    if (h->slice.guide) return MCLG_OK;
+    if (h->slice.record) return MCLG_OK;
     const uint32_t n_max = h->prm.slice_n_max ? h->prm.slice_n_max : kSliceDefaultN;
     std::vector<uint32_t> rowstart;
-    std::vector<uint16_t> guide;
+    std::vector<uint16_t> record;
     std::vector<uint64_t> secondary;
     try {
         build_slice_tables(n_max, h->prm.C, h->prm.lambda_num, h->prm.lambda_den,
-                           (h->prm.flags & MCLG_GALILEAN) != 0u, rowstart, guide,
+                           (h->prm.flags & MCLG_GALILEAN) != 0u, rowstart, record,
                            secondary);
     } catch (...) {
         return MCLG_ERR_NOMEM;
@@ -535,7 +562,7 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     MCLG_CK(cudaStreamSynchronize(h->stream));
     free_slice_tables(h);
     if (cudaMalloc(&h->d_rowstart, rowstart.size() * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_slice_guide, guide.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_slice_record, record.size() * sizeof(uint16_t)) != cudaSuccess ||
         cudaMalloc(&h->d_slice_secondary, secondary.size() * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_heavy_pos, kHeavyCap * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&h->d_heavy_ctl, 3 * sizeof(uint32_t)) != cudaSuccess) {
@@ -545,19 +572,19 @@ mclg_status ensure_slice_tables(mclg_ctx *h)
     }
     MCLG_CK(cudaMemcpy(h->d_rowstart, rowstart.data(), rowstart.size() * sizeof(uint32_t),
                        cudaMemcpyHostToDevice));
-    MCLG_CK(cudaMemcpy(h->d_slice_guide, guide.data(), guide.size() * sizeof(uint16_t),
+    MCLG_CK(cudaMemcpy(h->d_slice_record, record.data(), record.size() * sizeof(uint16_t),
                        cudaMemcpyHostToDevice));
     MCLG_CK(cudaMemcpy(h->d_slice_secondary, secondary.data(), secondary.size() * sizeof(uint64_t),
                        cudaMemcpyHostToDevice));
     h->slice.n_max = n_max;
+    h->slice.rec_hb = n_max / 2 + 1;
     h->slice.rowstart = h->d_rowstart;
-    h->slice.guide = h->d_slice_guide;
+    h->slice.record = h->d_slice_record;
     h->slice.secondary = h->d_slice_secondary;
     MCLG_CK(cudaMemset(h->d_heavy_ctl, 0, 3 * sizeof(uint32_t)));
     h->slice.heavy_pos = h->d_heavy_pos;
     h->slice.heavy_ctl = h->d_heavy_ctl;
     h->slice.heavy_cap = kHeavyCap;
-    h->slice.guide_narrow = guide.size() <= size_t(0xFFFFFFFFu) ? 1u : 0u;
     drop_graphs(h);  // captured launches hold the old table pointers
     return MCLG_OK;
 }
@@ -766,7 +793,7 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
         // node pairs of the slice sampler's random numbers aligned with the lattice's
         if (replicas != 1 || (prm.flags & MCLG_STATS) || prm.mode == MCLG_MODE_PERSISTENT ||
             uint64_t(prm.node_offset) + L[0] > (uint64_t(1) << 32) ||
-            (prm.sampler == MCLG_SAMPLER_SLICE && (prm.node_offset & 1u)))
+            (prm.sampler == MCLG_SAMPLER_SLICE && (prm.node_offset & 7u)))
             return MCLG_ERR_ARG;
     } else if (prm.node_offset != 0) {
         return MCLG_ERR_ARG;
@@ -1186,7 +1213,7 @@ mclg_status mclg_halo_put(mclg_handle h, const uint16_t *in)
 
 mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32_t lambda_num,
                            uint32_t lambda_den, uint64_t *F, int32_t *dmin, int32_t *dmax,
-                           uint16_t *guide)
+                           uint16_t *record)
 {
     const uint32_t Jp = uint32_t(J < 0 ? -int64_t(J) : J);
     if (!F || !dmin || !dmax || C > uint32_t(kSliceMaxC) || N < 2 || Jp > N || b > N - Jp ||
@@ -1197,7 +1224,7 @@ mclg_status mclg_slice_row(uint32_t N, int32_t J, uint32_t b, uint32_t C, uint32
     if (8ull * uint64_t(N) * N * lambda_den >= kSliceMaxD) return MCLG_ERR_ARG;
     int lo = 0, hi = 0;
     build_slice_row(N, Jp, b, C, lambda_num, lambda_den, F, lo, hi);
-    if (guide) build_slice_guide(F, hi - lo, guide);
+    if (record) build_slice_record(F, hi - lo, -lo, record);
     *dmin = lo;
     *dmax = hi;
     return MCLG_OK;

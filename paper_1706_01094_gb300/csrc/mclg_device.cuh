@@ -14,7 +14,8 @@ namespace mclg {
 constexpr uint32_t kPurposeCollide = 0u;
 constexpr uint32_t kPurposeRefine = 1u;
 constexpr uint32_t kPurposeInit = 2u;
-constexpr uint32_t kPurposeSlice = 4u;
+constexpr uint32_t kPurposeSlice = 4u;     // slice sampler: the uniform's low 48 bits
+constexpr uint32_t kPurposeSliceTop = 6u;  // slice sampler: the uniform's top 16 bits
 constexpr int kChunksPerBlock = 10;  // 12-bit primary chunks in one 128-bit Philox block
 constexpr int kMaxRefine = 4;        // 16-bit refinement chunks allowed per decision
 

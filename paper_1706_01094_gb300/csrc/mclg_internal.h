@@ -16,15 +16,15 @@ constexpr uint32_t kMaxUnitReplicas = 512;       // replicas packed into one per
 constexpr uint32_t kMaxUnitNodes = 4096;         // longest replica kept in a persistent CTA
 constexpr uint32_t kPersistentVariants = 3;      // register bounds of the persistent kernel
 constexpr int kSliceMaxC = 10;                   // slice sampler: sub-collisions per step
-constexpr int kSliceBucketBits = 9;              // guide table: buckets of the top bits of Q
-constexpr int kSliceBuckets = 1 << kSliceBucketBits;
 constexpr int kSliceRowU64 = 20;                 // secondary row: 2C entries
-constexpr uint32_t kSliceMaxN = 1024;            // largest mass the slice tables may cover (rows < 2^32)
+constexpr int kSliceRecordLanes = 8;             // 15-bit values per 16-byte record
+constexpr uint32_t kSliceMaxN = 1024;            // largest mass the slice tables may cover (records < 2^32)
 constexpr uint64_t kSliceMaxD = uint64_t(1) << 44;  // exact-law denominator base D = 8 N^2 lambda_den
 constexpr uint32_t kSliceDefaultN = 256;         // slice tables' mass range unless set
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
-constexpr uint32_t kSliceVariants = 10;          // slice-kernel launch variants (see launch_slice)
-constexpr uint32_t kSliceClassicVariants = 6;    // of which k_step_slice; the rest k_step_slice_ws
+constexpr uint32_t kSliceVariants = 18;          // slice-kernel launch variants (see launch_slice)
+constexpr uint32_t kSliceTbFirst = 14;           // of which the temporally blocked ones: 14 ..
+constexpr uint32_t kSliceClassicVariants = 6;    // of which k_step_slice; the rest single-replica forms
 
 // Device-resident description of the internal replica order.
 struct Layout {
@@ -69,18 +69,18 @@ struct Unit {
 };
 
 struct SliceTables {
-    uint32_t n_max;             // rows cover 2 <= N <= n_max
-    const uint32_t *rowstart;   // [(n_max + 1)^2]
-    // [rows][kSliceBuckets]: bits 0-4 the number of entries below the bucket,
-    // bits 5-6 min(entries inside it, 3), bits 8-15 the next 8 bits (56..48)
-    // of the entry when it is the only one inside
-    const uint16_t *guide;
+    uint32_t n_max;             // tables cover N <= n_max (N < 2: identity)
+    uint32_t rec_hb;            // n_max / 2 + 1: records per (N, |J|)
+    const uint32_t *rowstart;   // [(n_max + 1)^2] first row of each (N, |J|) slice
+    // [(n_max + 1)^2 rec_hb] the 16-byte record of state (N, |J|, b) at
+    // (N (n_max + 1) + |J|) rec_hb + b / 2: lane j (16 bits, half j & 1 of
+    // word j / 2) holds the top 15 bits of F[c0 - 4 + j] (see mclg_slice.cuh)
+    const uint4 *record;
     const unsigned long long *secondary;  // [rows][kSliceRowU64]
     // nodes heavier than n_max, left for the sequential pass of the same step
     unsigned long long *heavy_pos;  // [heavy_cap] device-form node positions
     uint32_t *heavy_ctl;            // {count, overflow, blocks done}, zero between steps
     uint32_t heavy_cap;
-    uint32_t guide_narrow;          // 1: every guide index fits 32 bits (rows < 2^32 / buckets)
 };
 
 struct PersistentArgs {
@@ -131,12 +131,19 @@ cudaError_t launch_plain(const PlainArgs &p, bool one, cudaStream_t s);
 // Slice sampler (the C sub-collisions of a node drawn at once from tables).
 uint64_t slice_rows(uint32_t n_max);
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d, bool galilean,
-                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
+                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &record,
                         std::vector<uint64_t> &secondary);
+uint64_t slice_records(uint32_t n_max);
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
 constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass (usually empty)
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
-void build_slice_guide(const uint64_t *F, int n, uint16_t *guide);
+// Temporally blocked slice steps of one replica: n_steps <= slice_tb_steps(config)
+// steps in one launch, from p.in to p.out (heavy nodes collided in place).
+constexpr uint32_t kSliceTbConfigs = 4;
+uint32_t slice_tb_steps(uint32_t config);
+cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
+                            uint32_t config, cudaStream_t s);
+void build_slice_record(const uint64_t *F, int n, int c0, uint16_t *record);
 uint32_t slice_variant_vec(uint32_t variant);
 void build_slice_row(uint32_t N, uint32_t J, uint32_t b, uint32_t C, uint32_t lam_n, uint32_t lam_d,
                      uint64_t *F, int &dmin, int &dmax);

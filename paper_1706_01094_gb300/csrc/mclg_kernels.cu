@@ -127,10 +127,10 @@ __global__ void __launch_bounds__(kPlainThreads, kMinBlocks)
 // one barrier per step.  Each thread updates node pairs (2i, 2i+1), which never
 // straddle a replica because replicas start on multiples of 8 nodes.  kSlice:
 // the slice sampler (one table draw per node for masses up to the tables'
-// n_max, the node pair sharing one Philox block; the sequential draws above
-// it), with the tables' indices in 32 bits when kNarrow.
+// n_max, the node pair's top bits from one word of its eight-node group's
+// Philox block; the sequential draws above it).
 // ---------------------------------------------------------------------------
-template <int kMinBlocks, bool kSlice, bool kNarrow>
+template <int kMinBlocks, bool kSlice>
 __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_persistent(PersistentArgs p)
 {
     const bool kStream = p.stream != 0u;
@@ -201,11 +201,15 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_pers
                 uint32_t ln, ld;
                 bool seq0 = true, seq1 = true;
                 if (kSlice) {
-                    // x is even: the pair's Philox block, words (0, 1) and (2, 3)
-                    uint32_t w0 = x >> 1, w1 = rid, w2 = t, w3 = kPurposeSlice << 28;
-                    philox4x32_10(w0, w1, w2, w3, p.rk);
-                    seq0 = slice_node<kNarrow>(a0, b0, c0, w0, w1, p.tab, p.C, err);
-                    seq1 = slice_node<kNarrow>(a1, b1, c1, w2, w3, p.tab, p.C, err);
+                    // x is even: the pair's top bits are the two halves of one
+                    // word of its eight-node group's block
+                    uint32_t w[4];
+                    slice_top_block(x, rid, t, p.rk, w);
+                    const uint32_t word = pick_word(w, (x >> 1) & 3u);
+                    seq0 = slice_node(a0, b0, c0, word & 0xFFFFu, SliceKey{x, rid, t, p.k0, p.k1},
+                                      p.tab, p.C, err);
+                    seq1 = slice_node(a1, b1, c1, word >> 16, SliceKey{x + 1u, rid, t, p.k0, p.k1},
+                                      p.tab, p.C, err);
                 }
                 if (seq0) {
                     node_rate(p.galilean != 0u, a0, b0, c0, p.lam_n, p.lam_d, ln, ld);
@@ -577,9 +581,7 @@ static cudaError_t launch_persistent_v(const PersistentArgs &p, uint32_t n_units
                                        cudaStream_t s)
 {
     const size_t smem = persistent_smem_bytes(p.cap);
-    auto kern = !p.slice ? k_step_persistent<kMinBlocks, false, false>
-                         : (p.tab.guide_narrow ? k_step_persistent<kMinBlocks, true, true>
-                                               : k_step_persistent<kMinBlocks, true, false>);
+    auto kern = p.slice ? k_step_persistent<kMinBlocks, true> : k_step_persistent<kMinBlocks, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // as many CTAs as can be resident at once; they pull the units

@@ -10,14 +10,14 @@
 //
 // One thread takes V consecutive nodes of a replica (V = 2, 4, 8: one 4-, 8-
 // or 16-byte vector per plane; replicas start on multiples of 8 nodes, so a
-// vector never straddles two).  Node pair (2i, 2i + 1) shares one Philox
-// block: node 2i takes words (0, 1), node 2i + 1 words (2, 3) as Q.  The
-// row's guide entry for the top 9 bits of Q gives the count directly unless
-// an F[k] falls inside Q's bucket (about 1.6% of nodes near equilibrium); then
-// the entry also holds that F[k]'s next 8 bits, which decide Q against it
-// unless Q has the same 17 top bits (or several entries share the bucket,
-// mostly in the tails): then Q is compared with the row's u64 entries from
-// the guide's count on (about 0.5% of nodes near equilibrium).
+// vector never straddles two).  Eight consecutive nodes take the top 16 bits
+// of their uniforms Q from one Philox block.  The state's 16-byte record (the
+// top 15 bits of the eight F values around d = 0) decides the draw from Q's
+// top 15 bits unless d lies beyond +-3 or a prefix ties (about 0.2% of nodes
+// near equilibrium); then the rest of Q is drawn and Q compared with the
+// row's u64 entries (mclg_slice.cuh).  The records of the states a lattice
+// near equilibrium visits take a few hundred kilobytes, so most lookups hit
+// the SM's L1 cache.
 //
 // A node heavier than the tables' n_max takes the sequential sampler's C
 // decisions (the bits that sampler gives it) in a second, small pass of the
@@ -37,25 +37,13 @@
 
 namespace mclg {
 
-// The exact finish of a draw whose guide entry leaves Q undecided: compare Q
-// with the row's u64 values from `count` on.  Returns the final count; sets
-// the sampler error bit on a tie.
-__device__ __noinline__ uint32_t slice_finish(uint32_t count, uint32_t nvalid, uint64_t Q,
-                                              const unsigned long long *F, uint32_t &err)
-{
-    uint64_t f = 0;
-    while (count < nvalid && (f = __ldg(F + count)) < Q) ++count;
-    if (count < nvalid && f == Q) err |= kErrSampler;
-    return count;
-}
-
 // The table draws of one thread's V consecutive nodes [x0, x0 + V) of a
 // replica (nv of them valid, the rest padding that stays empty), from the
 // streamed planes em, e0, ep (device form) and the two halo values: nxt =
 // B_-1(x0 + V) and prv = B_+1(x0 - 1), periodic.  Writes the post-collision
-// values; returns a bit per node left for the heavy-node pass.  Node by node
-// (slice_node), one Philox block per node pair.
-template <int V, bool kNarrow>
+// values; returns a bit per node left for the heavy-node pass.  One Philox
+// block per node pair (slice_draws).
+template <int V>
 __device__ __forceinline__ uint32_t slice_vector(const uint32_t (&em)[V], const uint32_t (&e0)[V],
                                                  const uint32_t (&ep)[V], uint32_t nxt,
                                                  uint32_t prv, bool stream, uint32_t x0,
@@ -64,47 +52,28 @@ __device__ __forceinline__ uint32_t slice_vector(const uint32_t (&em)[V], const 
                                                  uint32_t (&om)[V], uint32_t (&o0)[V],
                                                  uint32_t (&op)[V], uint32_t &err)
 {
-    uint32_t heavy = 0;
+    // pre-collision occupations n_i(x) = B_i(x - v_i); padding stays empty
 #pragma unroll
-    for (int i = 0; i < V / 2; ++i) {
-        uint32_t w0 = (x0 >> 1) + uint32_t(i), w1 = r, w2 = t, w3 = kPurposeSlice << 28;
-        philox4x32_10(w0, w1, w2, w3, p.rk);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = 2 * i + h;
-            // pre-collision occupations n_i(x) = B_i(x - v_i); padding stays empty
-            uint32_t a, b, c;
-            if (stream) {
-                a = (uint32_t(j) + 1u < nv) ? em[(j + 1) % V] : nxt;
-                c = (j > 0) ? ep[(j + V - 1) % V] : prv;
-            } else {
-                a = em[j];
-                c = ep[j];
-            }
-            b = e0[j];
-            if (uint32_t(j) >= nv) a = b = c = 0u;
-            if (slice_node<kNarrow>(a, b, c, h ? w2 : w0, h ? w3 : w1, tab, p.C, err))
-                heavy |= 1u << j;
-            om[j] = a;
-            o0[j] = b;
-            op[j] = c;
+    for (int j = 0; j < V; ++j) {
+        if (stream) {
+            om[j] = (uint32_t(j) + 1u < nv) ? em[(j + 1) % V] : nxt;
+            op[j] = (j > 0) ? ep[(j + V - 1) % V] : prv;
+        } else {
+            om[j] = em[j];
+            op[j] = ep[j];
         }
+        o0[j] = e0[j];
+        if (uint32_t(j) >= nv) om[j] = o0[j] = op[j] = 0u;
     }
-    return heavy;
+    return slice_draws<V>(om, o0, op, x0, r, t, p.rk, p.k0, p.k1, tab, p.C, err);
 }
 
-// The same draws as slice_vector, with the work in phases over all V nodes so
-// that each thread has V table loads in flight at once: the row starts of
-// every node, the Philox blocks (while those loads are out), the guide
-// entries, then a branch-free decoding; the rare draws that the guide leaves
-// open are finished on the u64 values afterwards, in one branch per thread.
-// Nodes with N < 2 or beyond the tables load nothing and keep their state.
-//
-// `inputs_used` runs once the row-start loads, whose addresses depend on every
-// input value (the halo values included), have been issued: by then the
-// inputs have arrived in registers, so their shared-memory stage can be
+// The same draws as slice_vector for a full or partial vector read from a
+// shared-memory stage: `inputs_used` runs once the record loads, whose
+// addresses depend on every input value (the halo values included), have been
+// issued: by then the inputs have arrived in registers, so their stage can be
 // handed back.
-template <int V, bool kNarrow, typename InputsUsed>
+template <int V, typename InputsUsed>
 __device__ __forceinline__ uint32_t slice_vector_phased(
     const uint32_t (&em)[V], const uint32_t (&e0)[V], const uint32_t (&ep)[V], uint32_t nxt,
     uint32_t prv, bool stream, uint32_t x0, uint32_t nv, uint32_t r, uint32_t t, const PlainArgs &p,
@@ -126,71 +95,7 @@ __device__ __forceinline__ uint32_t slice_vector_phased(
             if (uint32_t(j) >= nv) om[j] = o0[j] = op[j] = 0u;
         }
     }
-    uint32_t heavy = 0, on = 0;  // bit j: node j beyond the tables / drawn from them
-    uint32_t rs[V];
-    const uint32_t stride = tab.n_max + 1u;
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        const uint32_t a = om[j], b = o0[j], c = op[j];
-        const uint32_t N = a + b + c, Jp = a > c ? a - c : c - a;
-        const bool drawn = N >= 2u && N <= tab.n_max;
-        heavy |= uint32_t(N > tab.n_max) << j;
-        on |= uint32_t(drawn) << j;
-        rs[j] = __ldg(tab.rowstart + (drawn ? N * stride + Jp : 0u));
-    }
-    inputs_used();
-    uint32_t lo[V], hi[V];
-#pragma unroll
-    for (int i = 0; i < V / 2; ++i) {
-        uint32_t w0 = (x0 >> 1) + uint32_t(i), w1 = r, w2 = t, w3 = kPurposeSlice << 28;
-        philox4x32_10(w0, w1, w2, w3, p.rk);
-        lo[2 * i] = w0;
-        hi[2 * i] = w1;
-        lo[2 * i + 1] = w2;
-        hi[2 * i + 1] = w3;
-    }
-    uint32_t e[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        // a state's row within its (N, |J|) slice is b / 2 (b has the parity of N - |J|)
-        rs[j] += o0[j] >> 1;
-        const uint32_t bucket = hi[j] >> (32 - kSliceBucketBits);
-        const bool drawn = (on >> j) & 1u;
-        e[j] = kNarrow
-            ? __ldg(tab.guide + (drawn ? rs[j] * uint32_t(kSliceBuckets) + bucket : 0u))
-            : __ldg(tab.guide + (drawn ? (uint64_t(rs[j]) << kSliceBucketBits) + bucket : 0ull));
-    }
-    uint32_t open = 0;  // bit j: the guide entry leaves node j's draw undecided
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        const uint32_t inside = (e[j] >> 5) & 3u;  // entries in Q's bucket (3: three or more)
-        const uint32_t qn = (hi[j] >> (24 - kSliceBucketBits)) & 0xFFu, fn = e[j] >> 8;
-        const bool one = inside == 1u && qn != fn;  // the next 8 bits decide Q against it
-        open |= uint32_t(inside != 0u && !one) << j;
-        e[j] = (e[j] & 0x1Fu) + uint32_t(one && qn > fn);  // the count so far
-    }
-    open &= on;
-    if (open) {
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            if (!((open >> j) & 1u)) continue;
-            const uint32_t a = om[j], b = o0[j], c = op[j];
-            const uint32_t Jp = a > c ? a - c : c - a;
-            const uint32_t nvalid = min(p.C, (a + c - Jp) >> 1) + min(p.C, b >> 1);
-            e[j] = slice_finish(e[j], nvalid, (uint64_t(hi[j]) << 32) | lo[j],
-                                tab.secondary + uint64_t(rs[j]) * kSliceRowU64, err);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        // d = dmin + count with dmin = -min(C, b / 2): b' = b + 2 d and, with N and
-        // J kept, a' = a - d, c' = c - d (arithmetic modulo 2^32)
-        const uint32_t d = ((on >> j) & 1u) ? e[j] - min(p.C, o0[j] >> 1) : 0u;
-        om[j] -= d;
-        o0[j] += 2u * d;
-        op[j] -= d;
-    }
-    return heavy;
+    return slice_draws<V>(om, o0, op, x0, r, t, p.rk, p.k0, p.k1, tab, p.C, err, inputs_used);
 }
 
 // Append the warp's heavy nodes (bit j of `heavy`: node node0 + j) to the list
@@ -220,7 +125,7 @@ __device__ __forceinline__ void list_heavy(uint32_t heavy, uint64_t node0, uint3
 // table); the kernel runs CTAs of kSliceThreads.  kStream: pull-stream before
 // colliding (else collide only).  kOne: a single replica, whose node indices
 // fit 32 bits.
-template <int V, int kMinBlocks, bool kOne, bool kNarrow, bool kStream>
+template <int V, int kMinBlocks, bool kOne, bool kStream>
 __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThreads)
     k_step_slice(PlainArgs p, SliceTables tab)
 {
@@ -273,7 +178,7 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
 
     uint32_t err = 0;
     uint32_t om[V], o0[V], op[V];
-    uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv,
+    uint32_t heavy = slice_vector<V>(em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv,
                                               rid + p.r0, t, p, tab, om, o0, op, err);
     if (active) {
         T vo;
@@ -288,6 +193,287 @@ __global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThread
     // heavy nodes (written unchanged) join the list of the sequential pass
     if (!active) heavy = 0u;
     list_heavy<V>(heavy, uint64_t(node0), lane, tab);
+}
+
+// ---------------------------------------------------------------------------
+// Grid-stride form for one replica (the single-lattice step): a grid sized to
+// the resident CTAs; each warp walks tiles of 32 V nodes, loading the next
+// tile's three vectors (and its edge values) into registers before it draws
+// the current one, so the HBM latency overlaps the table lookups.  The
+// per-launch values (round keys, table pointers) stay in registers for all of
+// a warp's tiles.
+// ---------------------------------------------------------------------------
+template <int V, int kMinBlocks, bool kStream>
+__global__ void __launch_bounds__(kSliceThreads, kMinBlocks * 256 / kSliceThreads)
+    k_step_slice_loop(PlainArgs p, SliceTables tab)
+{
+    static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
+    using T = typename VecT<V>::T;
+    constexpr uint32_t TW = 32u * uint32_t(V);  // nodes per warp tile
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t wpb = kSliceThreads / 32u;
+    const uint32_t wid = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    const uint64_t off = p.one_off;
+    const uint32_t L = p.one_L, Pn = (L + 7u) & ~7u;
+    const uint32_t tiles = (Pn + TW - 1u) / TW;
+    const uint16_t *__restrict__ inm = p.in + off;
+    const uint16_t *__restrict__ in0 = p.in + p.P + off;
+    const uint16_t *__restrict__ inp = p.in + 2 * p.P + off;
+    const uint32_t t = p.t_dev ? *p.t_dev + p.t : p.t;
+    const uint32_t r = p.one_rid + p.r0;
+    uint32_t err = 0;
+
+    // a tile's three vectors for this lane (lanes past the replica mirror its
+    // last vector and store nothing) and the edge values the lane needs from
+    // beyond its warp: B_-1(x0 + V) for the last lane (or the replica's end),
+    // B_+1(x0 - 1) for the first (or the replica's start)
+    auto load = [&](uint32_t tile, T &vm, T &vz, T &vp, uint32_t &hn, uint32_t &hp) {
+        const uint32_t x0 = tile * TW + lane * uint32_t(V);
+        const uint32_t xs = x0 < Pn ? x0 : Pn - uint32_t(V);
+        vm = __ldcs(reinterpret_cast<const T *>(inm + xs));
+        vz = __ldcs(reinterpret_cast<const T *>(in0 + xs));
+        vp = __ldcs(reinterpret_cast<const T *>(inp + xs));
+        hn = hp = 0u;
+        if (kStream && !(lane < 31u && x0 + V < L))
+            hn = x0 + V < L ? inm[x0 + V] : (p.halo_in ? p.halo_in[1] : inm[0]);
+        if (kStream && !(lane > 0u && x0 > 0u))
+            hp = x0 > 0u && x0 - 1u < L ? inp[x0 - 1u] : (p.halo_in ? p.halo_in[0] : inp[L - 1u]);
+    };
+
+    uint32_t tile = wid;
+    T cm, cz, cp;
+    uint32_t chn = 0, chp = 0;
+    if (tile < tiles) load(tile, cm, cz, cp, chn, chp);
+    for (; tile < tiles; tile += nw) {
+        T nm, nz, np;
+        uint32_t nhn = 0, nhp = 0;
+        if (tile + nw < tiles) load(tile + nw, nm, nz, np, nhn, nhp);
+        const uint32_t x0 = tile * TW + lane * uint32_t(V);
+        uint32_t em[V], e0[V], ep[V];
+        unpack(cm, em);
+        unpack(cz, e0);
+        unpack(cp, ep);
+        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
+        uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
+        if (kStream && !(lane < 31u && x0 + V < L)) nxt = chn;
+        if (kStream && !(lane > 0u && x0 > 0u)) prv = chp;
+        const uint32_t nv = x0 >= L ? 0u : (L - x0 < uint32_t(V) ? L - x0 : uint32_t(V));
+        uint32_t om[V], o0[V], op[V];
+        uint32_t heavy = slice_vector<V>(em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv, r, t, p,
+                                         tab, om, o0, op, err);
+        const bool active = x0 < Pn;
+        if (active) {
+            T vo;
+            pack(om, vo);
+            __stcs(reinterpret_cast<T *>(p.out + off + x0), vo);
+            pack(o0, vo);
+            __stcs(reinterpret_cast<T *>(p.out + p.P + off + x0), vo);
+            pack(op, vo);
+            __stcs(reinterpret_cast<T *>(p.out + 2 * p.P + off + x0), vo);
+        } else {
+            heavy = 0u;
+        }
+        list_heavy<V>(heavy, off + x0, lane, tab);
+        cm = nm;
+        cz = nz;
+        cp = np;
+        chn = nhn;
+        chp = nhp;
+    }
+    flag_error(p.err, err);
+}
+
+template <int V, int kMinBlocks>
+static cudaError_t launch_slice_loop_v(const PlainArgs &p, const SliceTables &tab, cudaStream_t s)
+{
+    auto kern = p.stream ? k_step_slice_loop<V, kMinBlocks, true> : k_step_slice_loop<V, kMinBlocks, false>;
+    static int resident[2] = {0, 0};  // CTAs per SM of the two forms
+    int &res = resident[p.stream ? 1 : 0];
+    cudaError_t e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (res == 0) {
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, int(kSliceThreads), 0)) !=
+            cudaSuccess)
+            return e;
+        res = std::max(per_sm, 1);
+    }
+    const uint32_t Pn = (p.one_L + 7u) & ~7u;
+    const uint32_t tiles = (Pn + 32u * V - 1u) / (32u * V);
+    const uint32_t warps = kSliceThreads / 32u;
+    const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>((tiles + warps - 1u) / warps,
+                                                                    uint32_t(sms * res)));
+    kern<<<grid, kSliceThreads, 0, s>>>(p, tab);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Temporally blocked form for one replica: a CTA of kThreads threads holds a
+// window of E = kThreads V consecutive nodes of the periodic lattice in
+// registers (V per thread) and advances it up to K steps in one launch.  Each
+// step a node needs B_-1 of its right neighbour and B_+1 of its left one
+// (Sec. III streaming); inside a warp they come by shuffle, across warps
+// through a shared slot per warp (double-buffered by step parity, one barrier
+// per step).  The window's ends have no neighbours, so after s steps only
+// [s, E - s) holds the lattice's values; nodes outside that cone are set to
+// zero before each draw (they report nothing and never reach the tables'
+// fallback or the sequential draws).  After the launch's n <= K steps the
+// middle T = E - 2K nodes, the CTA's own tile, are written.  Every node's
+// random numbers depend on its global index and time step only, so the nodes
+// that two windows both compute get the same values; nodes beyond the tables
+// take the sequential draws in place.  The state crosses HBM once per launch
+// instead of once per step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t wrap_node(int64_t x, uint32_t L)
+{
+    const int64_t m = x % int64_t(L);
+    return uint32_t(m < 0 ? m + int64_t(L) : m);
+}
+
+template <int V, int K, int kThreads, int kMinCtas>
+__global__ void __launch_bounds__(kThreads, kMinCtas)
+    k_step_slice_tb(PlainArgs p, SliceTables tab, uint32_t n_steps)
+{
+    static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
+    static_assert(K % V == 0 && K % 2 == 0, "the halo holds whole vectors");
+    constexpr uint32_t E = uint32_t(kThreads) * V, TT = E - 2u * K, W = kThreads / 32;
+    static_assert(TT % 8u == 0u && TT > 0u, "tiles start on multiples of 8 nodes");
+    using T = typename VecT<V>::T;
+    __shared__ uint32_t s_first[2][W], s_last[2][W];  // per warp: B_-1 of its first node, B_+1 of its last
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t off = p.one_off;
+    const uint32_t L = p.one_L, Pn = (L + 7u) & ~7u;
+    const uint32_t x0 = blockIdx.x * TT;                 // the tile's first node
+    const uint32_t e0 = threadIdx.x * uint32_t(V);       // this thread's first window position
+    const int64_t xs = int64_t(x0) + int64_t(e0) - K;    // its node before wrapping
+    const bool plain = xs >= 0 && xs + V <= int64_t(L);  // no wrap inside (xs is even, a multiple of V)
+    const uint16_t *__restrict__ inm = p.in + off;
+    const uint16_t *__restrict__ in0 = p.in + p.P + off;
+    const uint16_t *__restrict__ inp = p.in + 2 * p.P + off;
+    uint32_t em[V], ez[V], ep[V], xj[V];
+    if (plain) {
+        unpack(__ldcs(reinterpret_cast<const T *>(inm + xs)), em);
+        unpack(__ldcs(reinterpret_cast<const T *>(in0 + xs)), ez);
+        unpack(__ldcs(reinterpret_cast<const T *>(inp + xs)), ep);
+#pragma unroll
+        for (int j = 0; j < V; ++j) xj[j] = uint32_t(xs) + uint32_t(j);
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            xj[j] = wrap_node(xs + j, L);
+            em[j] = inm[xj[j]];
+            ez[j] = in0[xj[j]];
+            ep[j] = inp[xj[j]];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) xj[j] += p.x_base;  // the random numbers' node index
+    const uint32_t t0 = p.t_dev ? *p.t_dev + p.t : p.t;
+    const uint32_t r = p.one_rid + p.r0;
+    const bool stream = p.stream != 0u;
+    uint32_t err = 0;
+    for (uint32_t s = 0; s < n_steps; ++s) {
+        const uint32_t t = t0 + s;
+        uint32_t a[V], b[V], c[V];
+        if (stream) {
+            if (lane == 0u) s_first[s & 1u][warp] = em[0];
+            if (lane == 31u) s_last[s & 1u][warp] = ep[V - 1];
+            __syncthreads();
+            uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
+            uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
+            if (lane == 31u) nxt = warp + 1u < W ? s_first[s & 1u][warp + 1u] : 0u;
+            if (lane == 0u) prv = warp > 0u ? s_last[s & 1u][warp - 1u] : 0u;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                a[j] = j + 1 < V ? em[j + 1] : nxt;
+                b[j] = ez[j];
+                c[j] = j > 0 ? ep[j - 1] : prv;
+            }
+            // outside the cone of valid values: nothing
+            if (e0 <= s || e0 + V + s >= E) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const uint32_t e = e0 + uint32_t(j);
+                    if (e < s + 1u || e + s + 1u >= E) a[j] = b[j] = c[j] = 0u;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                a[j] = em[j];
+                b[j] = ez[j];
+                c[j] = ep[j];
+            }
+        }
+        const uint32_t heavy =
+            plain ? slice_draws<V>(a, b, c, xj[0], r, t, p.rk, p.k0, p.k1, tab, p.C, err)
+                  : slice_draws_scattered<V>(a, b, c, xj, r, t, p.rk, p.k0, p.k1, tab, p.C, err);
+        if (heavy) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                if (!((heavy >> j) & 1u)) continue;
+                const NodeKey nk{xj[j], r, t, p.k0, p.k1};
+                uint32_t ln, ld;
+                node_rate(p.galilean != 0u, a[j], b[j], c[j], p.lam_n, p.lam_d, ln, ld);
+                collide_node(a[j], b[j], c[j], nk, p.rk, p.C, ln, ld, err);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            em[j] = a[j];
+            ez[j] = b[j];
+            ep[j] = c[j];
+        }
+    }
+    // the tile's own nodes (padding beyond the replica's end written as zero)
+    if (e0 >= K && e0 + V <= K + TT) {
+        const uint32_t x = x0 + e0 - K;
+        if (x < Pn) {
+            if (x + V > L) {
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    if (x + uint32_t(j) >= L) em[j] = ez[j] = ep[j] = 0u;
+            }
+            T vo;
+            pack(em, vo);
+            __stcs(reinterpret_cast<T *>(p.out + off + x), vo);
+            pack(ez, vo);
+            __stcs(reinterpret_cast<T *>(p.out + p.P + off + x), vo);
+            pack(ep, vo);
+            __stcs(reinterpret_cast<T *>(p.out + 2 * p.P + off + x), vo);
+        }
+    }
+    flag_error(p.err, err);
+}
+
+template <int V, int K, int kThreads, int kMinCtas>
+static cudaError_t launch_slice_tb_v(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
+                                     cudaStream_t s)
+{
+    constexpr uint32_t TT = uint32_t(kThreads) * V - 2u * K;
+    if (n_steps == 0u || n_steps > uint32_t(K)) return cudaErrorInvalidValue;
+    const uint32_t Pn = (p.one_L + 7u) & ~7u;
+    k_step_slice_tb<V, K, kThreads, kMinCtas><<<(Pn + TT - 1u) / TT, kThreads, 0, s>>>(p, tab, n_steps);
+    return cudaGetLastError();
+}
+
+// Temporally blocked configurations: (nodes per thread, steps per launch,
+// threads per CTA, minimum CTAs per SM).
+static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 8, 16};
+
+uint32_t slice_tb_steps(uint32_t config) { return kTbSteps[config < kSliceTbConfigs ? config : 0]; }
+
+cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
+                            uint32_t config, cudaStream_t s)
+{
+    switch (config) {
+    case 0: return launch_slice_tb_v<4, 16, 256, 4>(p, tab, n_steps, s);
+    case 1: return launch_slice_tb_v<4, 16, 512, 2>(p, tab, n_steps, s);
+    case 2: return launch_slice_tb_v<4, 8, 512, 2>(p, tab, n_steps, s);
+    default: return launch_slice_tb_v<8, 16, 256, 3>(p, tab, n_steps, s);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +561,7 @@ struct WsTile {
     static constexpr uint32_t kStage = 3u * kBuf;           // uint16 per stage
 };
 
-template <int W, int V, int S, int kMinBlocks, bool kNarrow>
+template <int W, int V, int S, int kMinBlocks>
 __global__ void __launch_bounds__((W + 1) * 32, kMinBlocks)
     k_step_slice_ws(PlainArgs p, SliceTables tab)
 {
@@ -468,7 +654,7 @@ __global__ void __launch_bounds__((W + 1) * 32, kMinBlocks)
         // the stage goes back to the producer once every lane's reads of it have
         // been consumed (arriving right after issuing the shared-memory loads let
         // the next bulk copy overwrite values still in flight)
-        uint32_t heavy = slice_vector_phased<V, kNarrow>(
+        uint32_t heavy = slice_vector_phased<V>(
             em, e0, ep, nxt, prv, kStream, p.x_base + x0, nv, r, t, p, tab, om, o0, op, err, [&]() {
                 __syncwarp();
                 if (lane == 0u) mbar_arrive(&empty[s]);
@@ -494,8 +680,7 @@ static cudaError_t launch_slice_ws_v(const PlainArgs &p, const SliceTables &tab,
 {
     using Tl = WsTile<W, V>;
     const size_t smem = size_t(S) * Tl::kStage * sizeof(uint16_t);
-    auto kern = tab.guide_narrow ? k_step_slice_ws<W, V, S, kMinBlocks, true>
-                                 : k_step_slice_ws<W, V, S, kMinBlocks, false>;
+    auto kern = k_step_slice_ws<W, V, S, kMinBlocks>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -538,7 +723,7 @@ __device__ __forceinline__ void node_quantities(uint32_t a, uint32_t b, uint32_t
     q[15] = c * a1; q[16] = c * b1; q[17] = c * c1;
 }
 
-template <int KR, bool kRed, bool kNarrow, bool kStream>
+template <int KR, bool kRed, bool kStream>
 __global__ void __launch_bounds__(256) k_step_slice_stats(PlainArgs p, SliceTables tab, StatsArgs sa)
 {
     static_assert(KR >= 1 && KR <= 16, "32-bit counters hold at most 16 products below 2^28");
@@ -583,7 +768,7 @@ __global__ void __launch_bounds__(256) k_step_slice_stats(PlainArgs p, SliceTabl
             nc[j] = kStream ? ((j > 0) ? ep[(j + V - 1) % V] : prv) : ep[j];
         }
         uint32_t om[V], o0[V], op[V];
-        uint32_t heavy = slice_vector<V, kNarrow>(em, e0, ep, nxt, prv, kStream, p.x_base + xv, nv,
+        uint32_t heavy = slice_vector<V>(em, e0, ep, nxt, prv, kStream, p.x_base + xv, nv,
                                                   r + p.r0, t, p, tab, om, o0, op, err);
         if (inside) {
             __stcs(reinterpret_cast<uint32_t *>(p.out + node0), om[0] | (om[1] << 16));
@@ -712,28 +897,24 @@ static void launch_slice_v(const PlainArgs &p, bool one, const SliceTables &tab,
 {
     const uint64_t threads = (p.g_end - p.g_begin) * (8u / V);
     const dim3 grid(uint32_t((threads + kSliceThreads - 1) / kSliceThreads));
-    const bool narrow = tab.guide_narrow != 0u, stream = p.stream != 0u;
-#define MCLG_SLICE_LAUNCH(ONE, NARROW, STREAM)                                                  \
-    if (one == ONE && narrow == NARROW && stream == STREAM)                                     \
-        k_step_slice<V, kMinBlocks, ONE, NARROW, STREAM><<<grid, kSliceThreads, 0, s>>>(p, tab);
-    MCLG_SLICE_LAUNCH(true, true, true)
-    MCLG_SLICE_LAUNCH(true, true, false)
-    MCLG_SLICE_LAUNCH(true, false, true)
-    MCLG_SLICE_LAUNCH(true, false, false)
-    MCLG_SLICE_LAUNCH(false, true, true)
-    MCLG_SLICE_LAUNCH(false, true, false)
-    MCLG_SLICE_LAUNCH(false, false, true)
-    MCLG_SLICE_LAUNCH(false, false, false)
-#undef MCLG_SLICE_LAUNCH
+    const bool stream = p.stream != 0u;
+    if (one && stream) k_step_slice<V, kMinBlocks, true, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    else if (one) k_step_slice<V, kMinBlocks, true, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    else if (stream) k_step_slice<V, kMinBlocks, false, true><<<grid, kSliceThreads, 0, s>>>(p, tab);
+    else k_step_slice<V, kMinBlocks, false, false><<<grid, kSliceThreads, 0, s>>>(p, tab);
 }
 
 // Slice-kernel variants 0-5: k_step_slice with (nodes per thread, minimum
 // CTAs of 256 threads per SM, i.e. a register bound); variants 6-9: the
 // warp-specialised k_step_slice_ws with (consumer warps, stages, minimum CTAs
-// per SM), 8 nodes per thread, for single-replica launches (a launch over
-// several replicas takes variant 4 instead).  The autotuner picks one per
-// handle; every variant gives the same bits.
-static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8, 8, 8, 8, 8};
+// per SM), 4 nodes per consumer thread; variants 10-13: the grid-stride
+// k_step_slice_loop with (nodes per thread, minimum CTAs of 256 threads per
+// SM); variants 14-17: the temporally blocked k_step_slice_tb (configurations
+// 0-3), which the step loop drives several steps per launch.  Variants 6-17
+// apply to single-replica launches (a launch over several replicas takes
+// variant 4 instead).  The autotuner picks one per handle; every variant gives
+// the same bits.
+static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8, 4, 4, 4, 4, 2, 4, 4, 8, 4, 4, 4, 8};
 
 uint32_t slice_variant_vec(uint32_t variant)
 {
@@ -744,7 +925,10 @@ cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, c
 {
     if (p.g_end == p.g_begin) return cudaSuccess;
     if (p.variant >= kSliceVariants) return cudaErrorInvalidValue;
-    const uint32_t v = (!one && p.variant >= kSliceClassicVariants) ? 4u : p.variant;
+    // the single-replica forms; the blocked one treats its replica as periodic,
+    // so a block of a larger lattice takes a classic variant
+    const bool other = !one || (p.variant >= kSliceTbFirst && p.halo_in);
+    const uint32_t v = (other && p.variant >= kSliceClassicVariants) ? 4u : p.variant;
     cudaError_t e = cudaSuccess;
     switch (v) {
     case 0: launch_slice_v<2, 8>(p, one, tab, s); break;  // <= 32 registers
@@ -757,7 +941,15 @@ cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, c
     case 6: e = launch_slice_ws_v<16, 4, 6, 2>(p, tab, s); break;  // <= 60 registers
     case 7: e = launch_slice_ws_v<4, 4, 8, 6>(p, tab, s); break;   // <= 68
     case 8: e = launch_slice_ws_v<8, 4, 6, 4>(p, tab, s); break;   // <= 56
-    default: e = launch_slice_ws_v<2, 4, 12, 10>(p, tab, s); break; // <= 68
+    case 9: e = launch_slice_ws_v<2, 4, 12, 10>(p, tab, s); break; // <= 68
+    // grid-stride form: (nodes per thread, minimum CTAs of 256 threads per SM)
+    case 10: e = launch_slice_loop_v<2, 6>(p, tab, s); break;  // <= 40 registers
+    case 11: e = launch_slice_loop_v<4, 5>(p, tab, s); break;  // <= 48
+    case 12: e = launch_slice_loop_v<4, 4>(p, tab, s); break;  // <= 64
+    case 13: e = launch_slice_loop_v<8, 3>(p, tab, s); break;  // <= 80
+    // temporally blocked form, one step (the step loop gives it more); heavy
+    // nodes are collided in place, so no second pass
+    default: return launch_slice_tb(p, tab, 1u, v - kSliceTbFirst, s);
     }
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
@@ -777,11 +969,8 @@ static void launch_slice_stats_v(const PlainArgs &p, const SliceTables &tab, con
 {
     const uint32_t Pn = (p.one_L + 7u) & ~7u;
     const dim3 grid((Pn + 63u) / 64u, (sa.R + 8u * KR - 1u) / (8u * KR));
-    const bool narrow = tab.guide_narrow != 0u, stream = p.stream != 0u;
-    if (narrow && stream) k_step_slice_stats<KR, kRed, true, true><<<grid, 256, 0, s>>>(p, tab, sa);
-    else if (narrow) k_step_slice_stats<KR, kRed, true, false><<<grid, 256, 0, s>>>(p, tab, sa);
-    else if (stream) k_step_slice_stats<KR, kRed, false, true><<<grid, 256, 0, s>>>(p, tab, sa);
-    else k_step_slice_stats<KR, kRed, false, false><<<grid, 256, 0, s>>>(p, tab, sa);
+    if (p.stream) k_step_slice_stats<KR, kRed, true><<<grid, 256, 0, s>>>(p, tab, sa);
+    else k_step_slice_stats<KR, kRed, false><<<grid, 256, 0, s>>>(p, tab, sa);
 }
 
 // Statistics-form configurations (replicas per warp, shared-memory counter

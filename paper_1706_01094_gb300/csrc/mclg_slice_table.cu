@@ -3,13 +3,13 @@
 // count after C sub-collisions (Sec. III, Sec. III.A: the C-th power of the
 // one-sub-collision matrix), as exact fixed-point values
 //     F[d] = min(floor(CDF[d] 2^64), 2^64 - 1),   d = dmin .. dmax - 1,
-// stored per row re-based at dmin (the u64 secondary table), and a guide
-// table that the kernel reads first: for each of the 2^9 buckets of the top
-// bits of a 64-bit uniform Q, the number of entries below the bucket's start,
-// how many lie inside it and, when exactly one does, its next 8 bits, which
-// decide Q against it unless Q shares them too; the rest is decided on the
-// u64 entries.  The law is symmetric under
-// J -> -J (it depends on a c and b only), so only J >= 0 is stored.
+// stored per row re-based at dmin (the u64 secondary table), and a 16-byte
+// record per state that the kernel reads first: the top 15 bits of the eight
+// values around d = 0 (F[c0 - 4 + j], j = 0..7, c0 = -dmin; 0 below the
+// row's first entry, 0x7FFF past its last), which decide almost every draw
+// (mclg_slice.cuh).  States with N < 2 get identity records.  The law is
+// symmetric under J -> -J (it depends on a c and b only), so only J >= 0 is
+// stored.
 //
 // Exact arithmetic: numerators over D^C with D = 8 N^2 lam_d, in fixed-size
 // unsigned big integers of 64-bit limbs.
@@ -219,32 +219,36 @@ uint64_t slice_rows(uint32_t n_max)
     return rows;
 }
 
-// Guide row of one law, for each bucket j = [j 2^55, (j + 1) 2^55):
-// below = #{k : F[k] < j 2^55}, inside = #{k : F[k] in bucket j};
-// entry = below | min(inside, 3) << 5 | (inside == 1 ? bits 54..47 of that F : 0) << 8.
-void build_slice_guide(const uint64_t *F, int n, uint16_t *guide)
+uint64_t slice_records(uint32_t n_max)
 {
-    constexpr int kShift = 64 - kSliceBucketBits;
-    int k = 0;
-    for (int j = 0; j < kSliceBuckets; ++j) {
-        while (k < n && (F[k] >> kShift) < uint64_t(j)) ++k;
-        int inside = 0;
-        while (k + inside < n && (F[k + inside] >> kShift) == uint64_t(j)) ++inside;
-        const uint32_t next8 = inside == 1 ? uint32_t(F[k] >> (kShift - 8)) & 0xFFu : 0u;
-        guide[j] = uint16_t(uint32_t(k) | uint32_t(inside < 3 ? inside : 3) << 5 | next8 << 8);
+    return uint64_t(n_max + 1) * (n_max + 1) * (n_max / 2 + 1);
+}
+
+// Record of one law with n entries, c0 = -dmin: lane j = the top 15 bits of
+// F[c0 - 4 + j], or 0 below the first entry and 0x7FFF past the last.
+void build_slice_record(const uint64_t *F, int n, int c0, uint16_t *record)
+{
+    for (int j = 0; j < kSliceRecordLanes; ++j) {
+        const int k = c0 - 4 + j;
+        record[j] = k < 0 ? uint16_t(0) : k >= n ? uint16_t(0x7FFF) : uint16_t(F[k] >> 49);
     }
 }
 
 // Fills rowstart[N * (n_max + 1) + J] (first row of the (N, J) slice),
-// guide[row * kSliceBuckets + j] and secondary[row * kSliceRowU64 + k].
+// secondary[row * kSliceRowU64 + k] and the records, 8 lanes each, of every
+// state (N, J, b) at (N (n_max + 1) + J) (n_max / 2 + 1) + b / 2.
 void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam_d, bool galilean,
-                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &guide,
+                        std::vector<uint32_t> &rowstart, std::vector<uint16_t> &record,
                         std::vector<uint64_t> &secondary)
 {
     const uint64_t rows = slice_rows(n_max);
+    const uint64_t hb = n_max / 2 + 1;
     rowstart.assign(size_t(n_max + 1) * (n_max + 1), 0u);
-    guide.assign(rows * kSliceBuckets, 0u);
     secondary.assign(rows * kSliceRowU64, UINT64_MAX);
+    // identity records (d = 0 whatever Q's top bits: no entries around c0 = 0)
+    record.resize(slice_records(n_max) * kSliceRecordLanes);
+    for (uint64_t i = 0; i < record.size(); ++i)
+        record[i] = (i % kSliceRecordLanes) < 4 ? uint16_t(0) : uint16_t(0x7FFF);
     uint64_t r = 0;
     for (uint32_t N = 0; N <= n_max; ++N)
         for (uint32_t J = 0; J <= N; ++J) {
@@ -272,7 +276,8 @@ void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam
                         build_row(uint32_t(N), J, b, sp, F, dmin, dmax);
                         const uint64_t row = first + (b - bmin) / 2;
                         for (int i = 0; i < dmax - dmin; ++i) secondary[row * kSliceRowU64 + i] = F[i];
-                        build_slice_guide(F, dmax - dmin, &guide[row * kSliceBuckets]);
+                        const uint64_t rec = (uint64_t(N) * (n_max + 1) + J) * hb + b / 2;
+                        build_slice_record(F, dmax - dmin, -dmin, &record[rec * kSliceRecordLanes]);
                     }
                 }
         });

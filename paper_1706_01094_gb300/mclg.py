@@ -337,17 +337,17 @@ def moments_noalloc(n, N=None, J=None, totals=None, stream=None) -> int:
                                         _stream_ptr(stream)))
 
 
-def slice_row(N: int, J: int, b: int, C: int = 10, lam=(1, 1), guide: bool = False):
+def slice_row(N: int, J: int, b: int, C: int = 10, lam=(1, 1), record: bool = False):
     """The library's slice-sampler table row (host computation): (F, dmin, dmax),
-    and the row's 512 guide entries as a fourth item when ``guide``."""
+    and the state's 8-lane record (uint16) as a fourth item when ``record``."""
     lib = load()
     F = np.zeros(2 * max(C, 1), dtype=np.uint64)
-    G = np.zeros(512, dtype=np.uint16)
+    R = np.zeros(8, dtype=np.uint16)
     dmin, dmax = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(lib.mclg_slice_row(N, J, b, C, lam[0], lam[1], _ptr(F), ctypes.byref(dmin),
-                              ctypes.byref(dmax), _ptr(G) if guide else None), "mclg_slice_row")
+                              ctypes.byref(dmax), _ptr(R) if record else None), "mclg_slice_row")
     out = (F[: dmax.value - dmin.value], int(dmin.value), int(dmax.value))
-    return out + (G,) if guide else out
+    return out + (R,) if record else out
 
 
 def philox(ctr, seed: int, out=None, stream=None):

@@ -63,11 +63,12 @@ def allreduce_sum_int64(values, group=None) -> np.ndarray:
     return t.numpy()
 
 
-def blocks(L: int, world: int, align: int = 2) -> list[tuple[int, int]]:
+def blocks(L: int, world: int, align: int = 8) -> list[tuple[int, int]]:
     """Contiguous node ranges [begin, end) of one periodic lattice of L nodes,
     one per rank, as equal as possible, every begin a multiple of `align` (the
-    slice sampler draws the random numbers of node pairs (2i, 2i + 1) together,
-    so its blocks start on even nodes).  Needs L >= world * align."""
+    slice sampler draws the top bits of eight consecutive nodes' uniforms from
+    one Philox block, so its blocks start on multiples of 8).  Needs
+    L >= world * align."""
     if world < 1 or align < 1:
         raise ValueError("world and align must be >= 1")
     if L < world * align:

@@ -28,6 +28,16 @@ def test_launch_counts_follow_the_library_schedule():
         == 3 * batched.replicas
     # sequential persistent: one launch per call of at most 65536 steps
     assert bench.count_launches(2000, batched, 0, True, False, MODES) == 1
+    # temporally blocked slice launches: 16 (or 8) steps each, two (four) per graph
+    assert bench.blocked_span({"plain_variant": 14}, single, False) == 16
+    assert bench.blocked_span({"plain_variant": 16}, single, False) == 8
+    assert bench.blocked_span({"plain_variant": 4}, single, False) == 1
+    assert bench.blocked_span({"plain_variant": 14}, single, True) == 1     # statistics form
+    assert bench.blocked_span({"plain_variant": 14}, batched, False) == 1   # several replicas
+    assert bench.count_launches(10000, single, 0, False, False, MODES, True, 16) \
+        == 312 * 2 + 312 + 1 + 1
+    assert bench.count_launches(20, single, 0, False, False, MODES, True, 16) == 2
+    assert bench.count_launches(64, single, 0, False, False, MODES, True, 8) == 8 + 2 + 1
 
 
 def test_default_sampler_per_workload():

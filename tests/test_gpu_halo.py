@@ -71,12 +71,12 @@ def test_one_block_with_crossed_exchange_is_the_periodic_lattice(sampler):
 
 @pytest.mark.parametrize("sampler,variant", [(SEQ, None), (SEQ, 1), (SEQ, 3), (SLICE, None),
                                              (SLICE, 0), (SLICE, 2), (SLICE, 5), (SLICE, 6),
-                                             (SLICE, 9)])
+                                             (SLICE, 9), (SLICE, 10), (SLICE, 13), (SLICE, 15)])
 def test_blocks_reproduce_the_lattice(sampler, variant):
-    """Four uneven blocks (one of 2 nodes, lengths not multiples of 8), every
-    launch shape of the per-step kernels."""
+    """Four uneven blocks (one of 8 nodes, the last of 3, lengths not all
+    multiples of 8), every launch shape of the per-step kernels."""
     L = 5003
-    cuts = [0, 1202, 1204, 3000, L]
+    cuts = [0, 1200, 1208, 5000, L]
     n0 = workloads.random_state([L], 33.0, seed=7)
     want = reference(L, 11, n0, 20, 13, sampler)
     got = run_blocks(L, cuts, 11, n0, 20, 13, sampler, kernel_variant=variant)
@@ -128,8 +128,8 @@ def test_halo_arguments_and_order_of_calls():
         mclg.Lattice(L, node_offset=0, flags=mclg.STATS)
     with pytest.raises(mclg.MCLGError):          # not the persistent mode
         mclg.Lattice(L, node_offset=0, mode=mclg.MODE_PERSISTENT)
-    with pytest.raises(mclg.MCLGError):          # slice sampler: blocks start on even nodes
-        mclg.Lattice(L, node_offset=3, sampler=SLICE)
+    with pytest.raises(mclg.MCLGError):          # slice sampler: blocks start on multiples of 8
+        mclg.Lattice(L, node_offset=12, sampler=SLICE)
     with pytest.raises(mclg.MCLGError):          # global indices below 2^32
         mclg.Lattice(L, node_offset=2**32 - 50)
     lib = mclg.load()

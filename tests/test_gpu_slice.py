@@ -108,12 +108,13 @@ def test_slice_full_size_sampled_nodes():
         assert after[2, (y + 1) % L] == nc      # v = +1 moved right
 
 
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", range(18))
 def test_slice_every_launch_variant_bit_exact(variant):
     """Each launch shape of the slice kernel (2, 4 or 8 nodes per thread, register
-    bounds; the warp-specialised form with bulk-copy stages for single-replica
-    launches) gives the oracle's bits, on ragged replicas whose ends fall inside a
-    thread's vector, on one long lattice, and without streaming."""
+    bounds; for single-replica launches the warp-specialised form with bulk-copy
+    stages, the grid-stride form and the temporally blocked form) gives the
+    oracle's bits, on ragged replicas whose ends fall inside a thread's vector, on
+    one long lattice, and without streaming."""
     L = [8, 3, 100, 1, 517, 64, 6]
     n0 = workloads.random_state(L, 40.0, seed=variant)
     want, err = oracle.slice_step(L, 5, n0, 2, 4)
@@ -126,7 +127,7 @@ def test_slice_every_launch_variant_bit_exact(variant):
     assert err == 0
     assert np.array_equal(run_slice([4099], 6, n1, 1, 3, kernel_variant=variant), want)
     with pytest.raises(mclg.MCLGError):
-        mclg.Lattice(L, sampler=SLICE, kernel_variant=10)  # ten variants: 0 .. 9
+        mclg.Lattice(L, sampler=SLICE, kernel_variant=18)  # eighteen variants: 0 .. 17
     for Ls in ([1], [7], [8], [1031], [3 * 4096 + 13]):     # tails inside a tile and a vector
         n2 = workloads.random_state(Ls, 45.0, seed=Ls[0])
         want, err = oracle.slice_step(Ls, 6, n2, 9, 5)
@@ -153,11 +154,12 @@ def test_slice_galilean_rate_bit_exact():
         assert np.array_equal(got, want), n_max
 
 
-@pytest.mark.parametrize("variant", [6, 7, 8, 9])
-def test_warp_specialised_ring_wraps_many_times(variant):
+@pytest.mark.parametrize("variant", range(6, 18))
+def test_single_replica_forms_walk_many_tiles(variant):
     """A lattice long enough that every CTA of the warp-specialised kernel cycles
-    through its ring of shared-memory stages several times (2^24 + 12345 nodes,
-    a tail inside the last tile and inside a vector), two steps, every node."""
+    through its ring of shared-memory stages several times, and every warp of the
+    grid-stride kernel walks many tiles (2^24 + 12345 nodes, a tail inside the
+    last tile and inside a vector), two steps, every node."""
     L = [(1 << 24) + 12345]
     n0 = workloads.random_state(L, 33.0, seed=variant)
     want, err = oracle.slice_step(L, 17, n0, 40, 2)
@@ -238,3 +240,45 @@ def test_slice_persistent_full_size_batch_prefix():
         got, _ = lat.get_state()
     bad = np.nonzero((got != want).any(axis=0))[0]
     assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
+
+
+# tiles of the temporally blocked configurations (window E = threads x nodes per
+# thread, halo K on each side): 992, 2016, 2032 and 2016 own nodes
+_TB_TILES = {14: 992, 15: 2016, 16: 2032, 17: 2016}
+
+
+@pytest.mark.parametrize("variant", [14, 15, 16, 17])
+def test_blocked_form_many_steps_bit_exact(variant):
+    """The temporally blocked form over many steps per launch: lattices shorter
+    than one window (it then wraps several times), of odd length (the random
+    numbers' node pairs straddle the wrap), one and two tiles with tails, and a
+    tile plus one node; step counts below, at and above the steps of one launch,
+    and past a 32-step graph replay."""
+    T = _TB_TILES[variant]
+    for L, steps in (([1], 3), ([2], 17), ([5], 9), ([33], 40), ([1000], 16), ([T], 5),
+                     ([T + 1], 17), ([2 * T + 37], 70), ([3 * T - 6], 33)):
+        n0 = workloads.random_state(L, 37.0, seed=L[0])
+        want, err = oracle.slice_step(L, 8, n0, 11, steps)
+        assert err == 0
+        got = run_slice(L, 8, n0, 11, steps, kernel_variant=variant)
+        bad = np.nonzero((got != want).any(axis=0))[0]
+        assert bad.size == 0, f"L={L} steps={steps}: {bad.size} nodes differ, first {bad[:5].tolist()}"
+
+
+@pytest.mark.parametrize("variant", [14, 17])
+def test_blocked_form_heavy_nodes_rates_and_no_stream(variant):
+    """Nodes beyond the tables collided in place by the sequential draws, the
+    Galilean rate, other C and lambda, and collide-only steps, over 40 steps."""
+    L = [3 * _TB_TILES[variant] + 11]
+    n0 = workloads.random_state(L, 40.0, seed=3)
+    want, err = oracle.slice_step(L, 4, n0, 0, 40, n_max=48)
+    assert err == 0
+    assert np.array_equal(run_slice(L, 4, n0, 0, 40, slice_n_max=48, kernel_variant=variant), want)
+    want, err = oracle.slice_step(L, 4, n0, 5, 40, C=3, lam=(3, 4), flags=oracle.FLAG_GALILEAN)
+    assert err == 0
+    got = run_slice(L, 4, n0, 5, 40, C=3, lam=(3, 4), flags=mclg.GALILEAN, kernel_variant=variant)
+    assert np.array_equal(got, want)
+    want, err = oracle.slice_step(L, 4, n0, 5, 40, flags=oracle.FLAG_NO_STREAM)
+    assert err == 0
+    got = run_slice(L, 4, n0, 5, 40, flags=mclg.NO_STREAM, kernel_variant=variant)
+    assert np.array_equal(got, want)

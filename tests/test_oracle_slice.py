@@ -139,9 +139,10 @@ def test_nodes_beyond_n_max_take_the_sequential_draws():
 
 
 def test_slice_uniform_bits_are_uniform_and_independent():
-    """Q (two words of a Philox block per node, two nodes per block) behaves as
-    uniform bits: each byte of Q is uniform over 256 values, neighbouring
-    nodes' top bytes are uncorrelated, and no two nodes share a prefix."""
+    """Q (its top 16 bits from a Philox block shared by eight nodes, the rest
+    from a block shared by two) behaves as uniform bits: each byte of Q is
+    uniform over 256 values, neighbouring nodes' top bytes are uncorrelated, and
+    no two nodes share a prefix."""
     qs = np.array([oracle.slice_q(x, 3, 7, 12345) for x in range(16384)], dtype=np.uint64)
     for shift in (56, 48, 40, 0):
         counts = np.bincount(((qs >> np.uint64(shift)) & np.uint64(0xFF)).astype(np.int64),
@@ -151,6 +152,24 @@ def test_slice_uniform_bits_are_uniform_and_independent():
     top = (qs >> np.uint64(56)).astype(np.float64)
     assert abs(np.corrcoef(top[:-1], top[1:])[0, 1]) < 0.04
     assert len(set(int(q) for q in qs)) == len(qs)
+
+
+def test_slice_uniform_layout_over_philox_blocks():
+    """Q's bits come from the oracle's Philox4x32-10 (pinned to cuRAND's host
+    generator) as the contract lays them out: the top 16 bits of nodes
+    8k .. 8k+7 read in order are the four words of block (k, r, t, 6 << 28),
+    low half first, and the next 48 bits of node x are the low 16 bits of word
+    1 (even x) or 3 (odd x) and word 0 or 2 of block (x // 2, r, t, 4 << 28)."""
+    seed, r, t = 987654321987, 5, 11
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for k in (0, 1, 77, 2**29 - 1):
+        top = [oracle.slice_q(8 * k + j, r, t, seed) >> 48 for j in range(8)]
+        w = oracle.philox([k, r, t, 6 << 28], key)
+        assert [int(v) for v in w] == [top[2 * i] | top[2 * i + 1] << 16 for i in range(4)]
+        for x in (8 * k, 8 * k + 3):
+            w = oracle.philox([x // 2, r, t, 4 << 28], key)
+            lo, mid = (w[0], w[1]) if x % 2 == 0 else (w[2], w[3])
+            assert oracle.slice_q(x, r, t, seed) & (2**48 - 1) == (int(mid) & 0xFFFF) << 32 | int(lo)
 
 
 def test_results_do_not_depend_on_thread_count_or_remembered_laws():

@@ -70,15 +70,18 @@ def test_two_rank_gloo_shards_reproduce_unsplit_batch(tmp_path):
         assert np.array_equal(np.load(tmp_path / f"tot_{r}.npy"), tot)
 
 
-def test_blocks_cover_the_lattice_on_even_starts():
-    for L, world in ((1000, 2), (1001, 3), (17, 8), (2**24, 8), (64, 1)):
-        parts = sharding.blocks(L, world)
+def test_blocks_cover_the_lattice_on_aligned_starts():
+    for L, world in ((1000, 2), (1001, 3), (64, 8), (2**24, 8), (64, 1), (17, 8)):
+        align = 8 if L >= 8 * world else 2
+        parts = sharding.blocks(L, world, align=align)
         assert parts[0][0] == 0 and parts[-1][1] == L and len(parts) == world
         for (b0, e0), (b1, e1) in zip(parts, parts[1:]):
-            assert e0 == b1 and b0 < e0 and b1 % 2 == 0
-        assert max(e - b for b, e in parts) <= L // world + 2
+            assert e0 == b1 and b0 < e0 and b1 % align == 0
+        assert max(e - b for b, e in parts) <= L // world + align
     with pytest.raises(ValueError):
         sharding.blocks(5, 3)
+    with pytest.raises(ValueError):
+        sharding.blocks(60, 8)      # fewer than 8 nodes per block
 
 
 def _halo_rank_main(rank, world, port, L, n0, steps, sampler, out_dir):

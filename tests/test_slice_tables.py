@@ -45,36 +45,38 @@ def test_rows_are_cumulative_and_symmetric(lib):
         lib.slice_row(10, 0, 4, C=11)  # the slice sampler draws at most 10 at once
 
 
-def test_guide_rows_count_entries_below_each_bucket(lib):
-    """Guide entry j of a row (bucket [j 2^55, (j+1) 2^55)) holds #{k : F[k] below
-    the bucket} (the oracle's F), min(#inside, 3) and, for a single entry inside,
-    its bits 54..47; a bucket with no entry decides #{k : Q > F[k]}, hence the new
-    rest count, for all Q in it, and one with a single entry decides every Q whose
-    bits 54..47 differ from the entry's."""
+def test_records_decide_draws_like_the_oracle(lib):
+    """Record lane j of a state holds the top 15 bits of the oracle's F[c0 - 4 + j]
+    (c0 = -dmin; 0 below the row, 0x7FFF past its end).  Wherever the record
+    decides (q = Q >> 49 equals no lane, lies above lane 0 and below lane 7),
+    every Q with those top bits draws d = #{lanes below q} - 4: checked with the
+    oracle's draw at the first and last Q of such prefixes, among them the
+    prefixes next to every lane."""
     rnd = random.Random(11)
-    for _ in range(120):
+    decided = 0
+    for _ in range(150):
         N = rnd.randint(2, 300)
         J = rnd.randint(-N, N)
         b = rnd.randrange((N - abs(J)) & 1, N - abs(J) + 1, 2)
         C = rnd.choice([1, 3, 10])
         lam = rnd.choice([(1, 1), (2, 5), (0, 1)])
-        F, dmin, dmax, G = lib.slice_row(N, J, b, C, lam, guide=True)
+        F, dmin, dmax, R = lib.slice_row(N, J, b, C, lam, record=True)
         Fo, omin, omax = oracle.slice_cdf(N, J, b, C, lam)
         Fo = [int(Fo[d + C]) for d in range(omin, omax)]
-        assert G.size == 512
-        for j in range(512):
-            below = sum(1 for f in Fo if f < j << 55)
-            ins = [f for f in Fo if j << 55 <= f < (j + 1) << 55]
-            next8 = (ins[0] >> 47) & 0xFF if len(ins) == 1 else 0
-            assert int(G[j]) == below | min(len(ins), 3) << 5 | next8 << 8, (N, J, b, C, lam, j)
-            if not ins:  # the count is the same for the bucket's first and last Q
-                for Q in (j << 55, ((j + 1) << 55) - 1):
-                    assert oracle.slice_draw(N, J, b, Q, C, lam) == b + 2 * (omin + below)
-            elif len(ins) == 1 and 0 < next8 < 255:  # Q's bits 54..47 decide against it
-                lo_q = (j << 55) | ((next8 - 1) << 47) | ((1 << 47) - 1)
-                hi_q = (j << 55) | ((next8 + 1) << 47)
-                assert oracle.slice_draw(N, J, b, lo_q, C, lam) == b + 2 * (omin + below)
-                assert oracle.slice_draw(N, J, b, hi_q, C, lam) == b + 2 * (omin + below + 1)
+        c0, n = -omin, omax - omin
+        lanes = [0 if k < 0 else 0x7FFF if k >= n else Fo[k] >> 49
+                 for k in (c0 - 4 + j for j in range(8))]
+        assert [int(v) for v in R] == lanes, (N, J, b, C, lam)
+        qs = {0, 1, 0x7FFE, 0x7FFF} | {rnd.randrange(0x8000) for _ in range(6)}
+        qs |= {t + e for t in lanes for e in (-1, 1) if 0 <= t + e <= 0x7FFF}
+        for q in sorted(qs):
+            g = sum(q >= t for t in lanes)
+            if q in lanes or not 1 <= g <= 7:
+                continue
+            decided += 1
+            for Q in (q << 49, ((q + 1) << 49) - 1):
+                assert oracle.slice_draw(N, J, b, Q, C, lam) == b + 2 * (g - 4), (N, J, b, Q)
+    assert decided > 500
 
 
 def test_rows_at_the_largest_accepted_denominators_equal_oracle(lib):
