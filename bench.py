@@ -397,9 +397,9 @@ def stats_merges(steps: int) -> int:
     return steps // GRAPH_STEPS + (1 if steps % GRAPH_STEPS else 0)
 
 
-# steps per launch of the slice sampler's temporally blocked variants (14 .. 17);
+# steps per launch of the slice sampler's temporally blocked variants (14 .. 19);
 # every other variant takes one step per launch
-SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 8, 17: 16}
+SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 4, 17: 8, 18: 16, 19: 8}
 
 
 def blocked_span(tuning, wl, stats_on) -> int:

@@ -135,11 +135,13 @@ typedef struct {
                                cores. */
     uint32_t kernel_variant; /* 0 = autotune the per-step kernel's launch variant at the first
                                 mclg_step; v + 1 = use variant v (SEQUENTIAL: 0 <= v < 6, nodes
-                                per thread and register bound; SLICE: 0 <= v < 14, 0-5 likewise,
+                                per thread and register bound; SLICE: 0 <= v < 20, 0-5 likewise,
                                 6-9 the warp-specialised form with bulk-copy staging, 10-13 a
                                 grid-stride form that loads each warp's next tile while it
-                                draws the current one; 6-13 apply to single-replica launches;
-                                reported by mclg_tuning).
+                                draws the current one, 14-19 a temporally blocked form that
+                                advances a window of nodes several steps per launch in
+                                registers; 6-19 apply to single-replica launches; reported by
+                                mclg_tuning).
                                 Every variant gives the same bits; this only fixes the launch
                                 shape. */
     uint32_t node_offset;    /* MCLG_HALO: index of the block's first node in the whole lattice

@@ -22,7 +22,7 @@ constexpr uint32_t kSliceMaxN = 1024;            // largest mass the slice table
 constexpr uint64_t kSliceMaxD = uint64_t(1) << 44;  // exact-law denominator base D = 8 N^2 lambda_den
 constexpr uint32_t kSliceDefaultN = 256;         // slice tables' mass range unless set
 constexpr uint32_t kPlainVariants = 6;           // plain-kernel launch variants (see launch_plain)
-constexpr uint32_t kSliceVariants = 18;          // slice-kernel launch variants (see launch_slice)
+constexpr uint32_t kSliceVariants = 20;          // slice-kernel launch variants (see launch_slice)
 constexpr uint32_t kSliceTbFirst = 14;           // of which the temporally blocked ones: 14 ..
 constexpr uint32_t kSliceClassicVariants = 6;    // of which k_step_slice; the rest single-replica forms
 
@@ -139,7 +139,7 @@ constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass 
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
 // Temporally blocked slice steps of one replica: n_steps <= slice_tb_steps(config)
 // steps in one launch, from p.in to p.out (heavy nodes collided in place).
-constexpr uint32_t kSliceTbConfigs = 4;
+constexpr uint32_t kSliceTbConfigs = 6;
 uint32_t slice_tb_steps(uint32_t config);
 cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
                             uint32_t config, cudaStream_t s);

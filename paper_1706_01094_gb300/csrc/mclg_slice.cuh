@@ -80,9 +80,62 @@ __device__ __forceinline__ uint32_t slice_top16(const uint32_t (&w)[4], uint32_t
 
 // The exact finish on the u64 values of the state's row (the record r left
 // the draw open): returns (d, error bits).  Q's low 48 bits come from node x's
-// pair block under the seed words (k0, k1).  The entries of the record's lanes
-// that lie strictly below q, and all entries before them, are below Q.  Every
-// argument is passed by value, so call sites keep their state in registers.
+// pair block under the seed words (k0, k1).  The record brackets the answer:
+// with gt lanes strictly below q and ge lanes at or below it, every entry up
+// to index c0 - 5 + gt lies below Q and entry c0 - 4 + ge above it, so the
+// count #{k : Q > F[k]} lies in [c0 - 4 + gt, c0 - 4 + ge] (clamped to the
+// row); it is found by scanning from the side the record bounds (usually one
+// or two loads).  Every argument is passed by value.
+__device__ __forceinline__ uint2 slice_exact_body(uint32_t N, uint32_t Jp, uint32_t b,
+                                                  uint32_t top16, uint32_t x, uint32_t rr,
+                                                  uint32_t t, uint32_t k0, uint32_t k1,
+                                                  const uint4 r, const uint32_t *rowstart,
+                                                  const unsigned long long *secondary,
+                                                  uint32_t n_max, uint32_t C)
+{
+    uint32_t w0 = x >> 1, w1 = rr, w2 = t, w3 = kPurposeSlice << 28;
+    philox4x32_10(w0, w1, w2, w3, k0, k1);
+    const bool odd = x & 1u;
+    const uint32_t lo = odd ? w2 : w0, hi = (top16 << 16) | ((odd ? w3 : w1) & 0xFFFFu);
+    const uint32_t below = b >> 1, above = (N - Jp - b) >> 1;
+    const int c0 = int(min(C, below)), nvalid = int(min(C, above)) + c0;
+    const uint32_t row = __ldg(rowstart + N * (n_max + 1u) + Jp) + below;
+    const unsigned long long *F = secondary + uint64_t(row) * kSliceRowU64;
+    const uint64_t Q = (uint64_t(hi) << 32) | lo;
+    const uint32_t q = hi >> 17, w[4] = {r.x, r.y, r.z, r.w};
+    int gt = 0, ge = 0;  // the lanes ascend, so both are prefixes
+#pragma unroll
+    for (int j = 0; j < kSliceRecordLanes; ++j) {
+        const uint32_t tj = (w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+        gt += q > tj;
+        ge += q >= tj;
+    }
+    const int kmin = gt > 0 ? max(0, min(nvalid, c0 - 4 + gt)) : 0;
+    const int kmax = ge < kSliceRecordLanes ? max(kmin, min(nvalid, c0 - 4 + ge)) : nvalid;
+    int count;
+    uint64_t f = 0;
+    bool seen = false;  // f = F[count] was loaded (and is >= Q)
+    if (gt > 0) {
+        // upward from the lower bound
+        for (count = kmin; count < kmax; ++count) {
+            f = __ldg(F + count);
+            if (f >= Q) {
+                seen = true;
+                break;
+            }
+        }
+    } else {
+        // downward from the upper bound
+        for (count = kmax; count > kmin; --count) {
+            const uint64_t g = __ldg(F + count - 1);
+            if (g < Q) break;
+            f = g;
+            seen = true;
+        }
+    }
+    return make_uint2(uint32_t(count - c0), (seen && f == Q) ? kErrSampler : 0u);
+}
+
 static __device__ __noinline__ uint2 slice_exact(uint32_t N, uint32_t Jp, uint32_t b,
                                                  uint32_t top16, uint32_t x, uint32_t rr,
                                                  uint32_t t, uint32_t k0, uint32_t k1,
@@ -90,24 +143,7 @@ static __device__ __noinline__ uint2 slice_exact(uint32_t N, uint32_t Jp, uint32
                                                  const unsigned long long *secondary,
                                                  uint32_t n_max, uint32_t C)
 {
-    uint32_t w0 = x >> 1, w1 = rr, w2 = t, w3 = kPurposeSlice << 28;
-    philox4x32_10(w0, w1, w2, w3, k0, k1);
-    const bool odd = x & 1u;
-    const uint32_t lo = odd ? w2 : w0, hi = (top16 << 16) | ((odd ? w3 : w1) & 0xFFFFu);
-    const uint32_t below = b >> 1, above = (N - Jp - b) >> 1;
-    const uint32_t c0 = min(C, below), nvalid = min(C, above) + c0;
-    const uint32_t row = __ldg(rowstart + N * (n_max + 1u) + Jp) + below;
-    const unsigned long long *F = secondary + uint64_t(row) * kSliceRowU64;
-    const uint64_t Q = (uint64_t(hi) << 32) | lo;
-    const uint32_t q = hi >> 17, w[4] = {r.x, r.y, r.z, r.w};
-    int gt = 0;  // lanes strictly below q (a prefix: the lanes ascend)
-#pragma unroll
-    for (int j = 0; j < kSliceRecordLanes; ++j) gt += q > ((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
-    const int start = gt > 0 ? int(c0) - 4 + gt : 0;
-    uint32_t count = start > 0 ? min(uint32_t(start), nvalid) : 0u;
-    uint64_t f = 0;
-    while (count < nvalid && (f = __ldg(F + count)) < Q) ++count;
-    return make_uint2(count - c0, (count < nvalid && f == Q) ? kErrSampler : 0u);
+    return slice_exact_body(N, Jp, b, top16, x, rr, t, k0, k1, r, rowstart, secondary, n_max, C);
 }
 
 // Node x's random-number identity: its global index, random-stream index and
@@ -199,14 +235,29 @@ __device__ __forceinline__ uint32_t slice_draws(uint32_t (&a)[V], uint32_t (&b)[
         d[j] = in ? g - 4u : 0u;
         open |= uint32_t(o && in) << j;
     }
-    if (open) {
+    // the open draws one at a time, inline: the node's values taken by
+    // selection, so nothing goes through local memory or a call
+    while (open) {
+        const uint32_t j = __ffs(open) - 1u;
+        open &= open - 1u;
+        uint32_t aj = a[0], bj = b[0], cj = c[0], tj = top[0];
+        uint4 rj = rec[0];
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            if (!((open >> j) & 1u)) continue;
-            const uint32_t N = a[j] + b[j] + c[j], Jp = a[j] > c[j] ? a[j] - c[j] : c[j] - a[j];
-            const SliceKey key{x0 + uint32_t(j), r, t, k0, k1};
-            d[j] = slice_exact_d(N, Jp, b[j], top[j], key, rec[j], tab, C, err);
-        }
+        for (int k = 1; k < V; ++k)
+            if (j == uint32_t(k)) {
+                aj = a[k];
+                bj = b[k];
+                cj = c[k];
+                tj = top[k];
+                rj = rec[k];
+            }
+        const uint32_t N = aj + bj + cj, Jp = aj > cj ? aj - cj : cj - aj;
+        const uint2 de = slice_exact_body(N, Jp, bj, tj, x0 + j, r, t, k0, k1, rj, tab.rowstart,
+                                          tab.secondary, tab.n_max, C);
+        err |= de.y;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (j == uint32_t(k)) d[k] = de.x;
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) {

@@ -332,21 +332,25 @@ __device__ __forceinline__ uint32_t wrap_node(int64_t x, uint32_t L)
     return uint32_t(m < 0 ? m + int64_t(L) : m);
 }
 
-template <int V, int K, int kThreads, int kMinCtas>
+// kWarp: every warp is a window of its own (E = 32 V, no barrier: a warp
+// that waits on a rare exact draw holds up nobody else); else the CTA is.
+template <int V, int K, int kThreads, int kMinCtas, bool kWarp>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
     k_step_slice_tb(PlainArgs p, SliceTables tab, uint32_t n_steps)
 {
     static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
     static_assert(K % V == 0 && K % 2 == 0, "the halo holds whole vectors");
-    constexpr uint32_t E = uint32_t(kThreads) * V, TT = E - 2u * K, W = kThreads / 32;
+    constexpr uint32_t E = uint32_t(kWarp ? 32 : kThreads) * V, TT = E - 2u * K, W = kThreads / 32;
     static_assert(TT % 8u == 0u && TT > 0u, "tiles start on multiples of 8 nodes");
     using T = typename VecT<V>::T;
     __shared__ uint32_t s_first[2][W], s_last[2][W];  // per warp: B_-1 of its first node, B_+1 of its last
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t off = p.one_off;
     const uint32_t L = p.one_L, Pn = (L + 7u) & ~7u;
-    const uint32_t x0 = blockIdx.x * TT;                 // the tile's first node
-    const uint32_t e0 = threadIdx.x * uint32_t(V);       // this thread's first window position
+    const uint32_t tile = kWarp ? blockIdx.x * W + warp : blockIdx.x;
+    const uint32_t x0 = tile * TT;                       // the tile's first node
+    const uint32_t e0 = (kWarp ? lane : threadIdx.x) * uint32_t(V);  // this thread's first window position
+    if (kWarp && x0 >= Pn) return;                       // a whole warp past the last tile
     const int64_t xs = int64_t(x0) + int64_t(e0) - K;    // its node before wrapping
     const bool plain = xs >= 0 && xs + V <= int64_t(L);  // no wrap inside (xs is even, a multiple of V)
     const uint16_t *__restrict__ inm = p.in + off;
@@ -378,13 +382,15 @@ __global__ void __launch_bounds__(kThreads, kMinCtas)
         const uint32_t t = t0 + s;
         uint32_t a[V], b[V], c[V];
         if (stream) {
-            if (lane == 0u) s_first[s & 1u][warp] = em[0];
-            if (lane == 31u) s_last[s & 1u][warp] = ep[V - 1];
-            __syncthreads();
+            if (!kWarp) {
+                if (lane == 0u) s_first[s & 1u][warp] = em[0];
+                if (lane == 31u) s_last[s & 1u][warp] = ep[V - 1];
+                __syncthreads();
+            }
             uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
             uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
-            if (lane == 31u) nxt = warp + 1u < W ? s_first[s & 1u][warp + 1u] : 0u;
-            if (lane == 0u) prv = warp > 0u ? s_last[s & 1u][warp - 1u] : 0u;
+            if (lane == 31u) nxt = !kWarp && warp + 1u < W ? s_first[s & 1u][warp + 1u] : 0u;
+            if (lane == 0u) prv = !kWarp && warp > 0u ? s_last[s & 1u][warp - 1u] : 0u;
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 a[j] = j + 1 < V ? em[j + 1] : nxt;
@@ -448,20 +454,23 @@ __global__ void __launch_bounds__(kThreads, kMinCtas)
     flag_error(p.err, err);
 }
 
-template <int V, int K, int kThreads, int kMinCtas>
+template <int V, int K, int kThreads, int kMinCtas, bool kWarp>
 static cudaError_t launch_slice_tb_v(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
                                      cudaStream_t s)
 {
-    constexpr uint32_t TT = uint32_t(kThreads) * V - 2u * K;
+    constexpr uint32_t TT = uint32_t(kWarp ? 32 : kThreads) * V - 2u * K;
+    constexpr uint32_t kPerCta = kWarp ? kThreads / 32 : 1;  // tiles per CTA
     if (n_steps == 0u || n_steps > uint32_t(K)) return cudaErrorInvalidValue;
     const uint32_t Pn = (p.one_L + 7u) & ~7u;
-    k_step_slice_tb<V, K, kThreads, kMinCtas><<<(Pn + TT - 1u) / TT, kThreads, 0, s>>>(p, tab, n_steps);
+    const uint32_t tiles = (Pn + TT - 1u) / TT;
+    k_step_slice_tb<V, K, kThreads, kMinCtas, kWarp>
+        <<<(tiles + kPerCta - 1u) / kPerCta, kThreads, 0, s>>>(p, tab, n_steps);
     return cudaGetLastError();
 }
 
 // Temporally blocked configurations: (nodes per thread, steps per launch,
-// threads per CTA, minimum CTAs per SM).
-static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 8, 16};
+// threads per CTA, minimum CTAs per SM, windows per warp or per CTA).
+static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 4, 8, 16, 8};
 
 uint32_t slice_tb_steps(uint32_t config) { return kTbSteps[config < kSliceTbConfigs ? config : 0]; }
 
@@ -469,10 +478,12 @@ cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t
                             uint32_t config, cudaStream_t s)
 {
     switch (config) {
-    case 0: return launch_slice_tb_v<4, 16, 256, 4>(p, tab, n_steps, s);
-    case 1: return launch_slice_tb_v<4, 16, 512, 2>(p, tab, n_steps, s);
-    case 2: return launch_slice_tb_v<4, 8, 512, 2>(p, tab, n_steps, s);
-    default: return launch_slice_tb_v<8, 16, 256, 3>(p, tab, n_steps, s);
+    case 0: return launch_slice_tb_v<4, 16, 256, 4, false>(p, tab, n_steps, s);
+    case 1: return launch_slice_tb_v<4, 16, 128, 8, false>(p, tab, n_steps, s);
+    case 2: return launch_slice_tb_v<4, 4, 256, 4, true>(p, tab, n_steps, s);
+    case 3: return launch_slice_tb_v<4, 8, 256, 4, true>(p, tab, n_steps, s);
+    case 4: return launch_slice_tb_v<4, 16, 128, 6, false>(p, tab, n_steps, s);
+    default: return launch_slice_tb_v<4, 8, 128, 8, false>(p, tab, n_steps, s);
     }
 }
 
@@ -909,12 +920,12 @@ static void launch_slice_v(const PlainArgs &p, bool one, const SliceTables &tab,
 // warp-specialised k_step_slice_ws with (consumer warps, stages, minimum CTAs
 // per SM), 4 nodes per consumer thread; variants 10-13: the grid-stride
 // k_step_slice_loop with (nodes per thread, minimum CTAs of 256 threads per
-// SM); variants 14-17: the temporally blocked k_step_slice_tb (configurations
-// 0-3), which the step loop drives several steps per launch.  Variants 6-17
+// SM); variants 14-19: the temporally blocked k_step_slice_tb (configurations
+// 0-5), which the step loop drives several steps per launch.  Variants 6-19
 // apply to single-replica launches (a launch over several replicas takes
 // variant 4 instead).  The autotuner picks one per handle; every variant gives
 // the same bits.
-static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8, 4, 4, 4, 4, 2, 4, 4, 8, 4, 4, 4, 8};
+static const uint32_t kSliceVec[kSliceVariants] = {2, 2, 4, 4, 8, 8, 4, 4, 4, 4, 2, 4, 4, 8, 4, 4, 4, 4, 4, 4};
 
 uint32_t slice_variant_vec(uint32_t variant)
 {

@@ -28,9 +28,10 @@ def test_launch_counts_follow_the_library_schedule():
         == 3 * batched.replicas
     # sequential persistent: one launch per call of at most 65536 steps
     assert bench.count_launches(2000, batched, 0, True, False, MODES) == 1
-    # temporally blocked slice launches: 16 (or 8) steps each, two (four) per graph
+    # temporally blocked slice launches: 16, 8 or 4 steps each, 2, 4 or 8 per graph
     assert bench.blocked_span({"plain_variant": 14}, single, False) == 16
-    assert bench.blocked_span({"plain_variant": 16}, single, False) == 8
+    assert bench.blocked_span({"plain_variant": 16}, single, False) == 4
+    assert bench.blocked_span({"plain_variant": 17}, single, False) == 8
     assert bench.blocked_span({"plain_variant": 4}, single, False) == 1
     assert bench.blocked_span({"plain_variant": 14}, single, True) == 1     # statistics form
     assert bench.blocked_span({"plain_variant": 14}, batched, False) == 1   # several replicas

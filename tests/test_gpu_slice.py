@@ -108,7 +108,7 @@ def test_slice_full_size_sampled_nodes():
         assert after[2, (y + 1) % L] == nc      # v = +1 moved right
 
 
-@pytest.mark.parametrize("variant", range(18))
+@pytest.mark.parametrize("variant", range(20))
 def test_slice_every_launch_variant_bit_exact(variant):
     """Each launch shape of the slice kernel (2, 4 or 8 nodes per thread, register
     bounds; for single-replica launches the warp-specialised form with bulk-copy
@@ -127,7 +127,7 @@ def test_slice_every_launch_variant_bit_exact(variant):
     assert err == 0
     assert np.array_equal(run_slice([4099], 6, n1, 1, 3, kernel_variant=variant), want)
     with pytest.raises(mclg.MCLGError):
-        mclg.Lattice(L, sampler=SLICE, kernel_variant=18)  # eighteen variants: 0 .. 17
+        mclg.Lattice(L, sampler=SLICE, kernel_variant=20)  # twenty variants: 0 .. 19
     for Ls in ([1], [7], [8], [1031], [3 * 4096 + 13]):     # tails inside a tile and a vector
         n2 = workloads.random_state(Ls, 45.0, seed=Ls[0])
         want, err = oracle.slice_step(Ls, 6, n2, 9, 5)
@@ -154,7 +154,7 @@ def test_slice_galilean_rate_bit_exact():
         assert np.array_equal(got, want), n_max
 
 
-@pytest.mark.parametrize("variant", range(6, 18))
+@pytest.mark.parametrize("variant", range(6, 20))
 def test_single_replica_forms_walk_many_tiles(variant):
     """A lattice long enough that every CTA of the warp-specialised kernel cycles
     through its ring of shared-memory stages several times, and every warp of the
@@ -242,12 +242,12 @@ def test_slice_persistent_full_size_batch_prefix():
     assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
 
 
-# tiles of the temporally blocked configurations (window E = threads x nodes per
-# thread, halo K on each side): 992, 2016, 2032 and 2016 own nodes
-_TB_TILES = {14: 992, 15: 2016, 16: 2032, 17: 2016}
+# tiles of the temporally blocked configurations (window E = threads of the CTA,
+# or of the warp, x nodes per thread; halo K on each side)
+_TB_TILES = {14: 992, 15: 480, 16: 120, 17: 112, 18: 480, 19: 496}
 
 
-@pytest.mark.parametrize("variant", [14, 15, 16, 17])
+@pytest.mark.parametrize("variant", range(14, 20))
 def test_blocked_form_many_steps_bit_exact(variant):
     """The temporally blocked form over many steps per launch: lattices shorter
     than one window (it then wraps several times), of odd length (the random
@@ -265,7 +265,7 @@ def test_blocked_form_many_steps_bit_exact(variant):
         assert bad.size == 0, f"L={L} steps={steps}: {bad.size} nodes differ, first {bad[:5].tolist()}"
 
 
-@pytest.mark.parametrize("variant", [14, 17])
+@pytest.mark.parametrize("variant", [14, 16, 19])
 def test_blocked_form_heavy_nodes_rates_and_no_stream(variant):
     """Nodes beyond the tables collided in place by the sequential draws, the
     Galilean rate, other C and lambda, and collide-only steps, over 40 steps."""
