@@ -399,7 +399,7 @@ def stats_merges(steps: int) -> int:
 
 # steps per launch of the slice sampler's temporally blocked variants (14 .. 19);
 # every other variant takes one step per launch
-SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 4, 17: 8, 18: 16, 19: 8}
+SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 4, 17: 8, 18: 16, 19: 16}
 
 
 def blocked_span(tuning, wl, stats_on) -> int:

@@ -332,19 +332,34 @@ __device__ __forceinline__ uint32_t wrap_node(int64_t x, uint32_t L)
     return uint32_t(m < 0 ? m + int64_t(L) : m);
 }
 
-// kWarp: every warp is a window of its own (E = 32 V, no barrier: a warp
-// that waits on a rare exact draw holds up nobody else); else the CTA is.
-template <int V, int K, int kThreads, int kMinCtas, bool kWarp>
+// kSync: how a window's warps meet each step.  kTbBarrier: the CTA is the
+// window, one barrier per step.  kTbWarp: every warp is a window of its own
+// (E = 32 V, nothing to wait for: a warp held up by a rare exact draw holds up
+// nobody else).  kTbNeighbours: the CTA is the window, and each warp waits
+// only for its two neighbours' edge values of the step (flags in shared
+// memory; the double-buffered slots let a warp run at most one step ahead of
+// a neighbour, which is what keeps a slot from being overwritten before it is
+// read); every wait gives up after kTbWaitCycles with MCLG_ERR_TIMEOUT.
+constexpr int kTbBarrier = 0, kTbWarp = 1, kTbNeighbours = 2;
+constexpr long long kTbWaitCycles = 2000000000ll;  // about a second
+
+template <int V, int K, int kThreads, int kMinCtas, int kSync>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
     k_step_slice_tb(PlainArgs p, SliceTables tab, uint32_t n_steps)
 {
+    constexpr bool kWarp = kSync == kTbWarp;
     static_assert(V == 2 || V == 4 || V == 8, "V nodes per thread: 2, 4 or 8");
     static_assert(K % V == 0 && K % 2 == 0, "the halo holds whole vectors");
     constexpr uint32_t E = uint32_t(kWarp ? 32 : kThreads) * V, TT = E - 2u * K, W = kThreads / 32;
     static_assert(TT % 8u == 0u && TT > 0u, "tiles start on multiples of 8 nodes");
     using T = typename VecT<V>::T;
     __shared__ uint32_t s_first[2][W], s_last[2][W];  // per warp: B_-1 of its first node, B_+1 of its last
+    __shared__ uint32_t s_flag[W];                     // kTbNeighbours: steps whose edges are out
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (kSync == kTbNeighbours) {
+        if (lane == 0u) s_flag[warp] = 0u;
+        __syncthreads();
+    }
     const uint64_t off = p.one_off;
     const uint32_t L = p.one_L, Pn = (L + 7u) & ~7u;
     const uint32_t tile = kWarp ? blockIdx.x * W + warp : blockIdx.x;
@@ -382,15 +397,41 @@ __global__ void __launch_bounds__(kThreads, kMinCtas)
         const uint32_t t = t0 + s;
         uint32_t a[V], b[V], c[V];
         if (stream) {
-            if (!kWarp) {
+            if (kSync == kTbBarrier) {
                 if (lane == 0u) s_first[s & 1u][warp] = em[0];
                 if (lane == 31u) s_last[s & 1u][warp] = ep[V - 1];
                 __syncthreads();
+            } else if (kSync == kTbNeighbours) {
+                if (lane == 0u) s_first[s & 1u][warp] = em[0];
+                if (lane == 31u) s_last[s & 1u][warp] = ep[V - 1];
+                __syncwarp();
+                bool ok = true;
+                if (lane == 0u) {
+                    volatile uint32_t *flag = s_flag;
+                    __threadfence_block();
+                    flag[warp] = s + 1u;  // this warp's edges of step s are out
+                    const long long start = clock64();
+                    while ((warp > 0u && flag[warp - 1u] < s + 1u) ||
+                           (warp + 1u < W && flag[warp + 1u] < s + 1u)) {
+                        if (clock64() - start > kTbWaitCycles) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence_block();
+                }
+                if (!__shfl_sync(0xFFFFFFFFu, ok ? 1u : 0u, 0)) {
+                    err |= kErrTimeout;  // a neighbour never came: give up (state unspecified)
+                    break;
+                }
+                __syncwarp();
             }
             uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, em[0], 1);
             uint32_t prv = __shfl_up_sync(0xFFFFFFFFu, ep[V - 1], 1);
-            if (lane == 31u) nxt = !kWarp && warp + 1u < W ? s_first[s & 1u][warp + 1u] : 0u;
-            if (lane == 0u) prv = !kWarp && warp > 0u ? s_last[s & 1u][warp - 1u] : 0u;
+            const volatile uint32_t *vf = &s_first[s & 1u][0], *vl = &s_last[s & 1u][0];
+            if (lane == 31u) nxt = !kWarp && warp + 1u < W ? vf[warp + 1u] : 0u;
+            if (lane == 0u) prv = !kWarp && warp > 0u ? vl[warp - 1u] : 0u;
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 a[j] = j + 1 < V ? em[j + 1] : nxt;
@@ -454,23 +495,24 @@ __global__ void __launch_bounds__(kThreads, kMinCtas)
     flag_error(p.err, err);
 }
 
-template <int V, int K, int kThreads, int kMinCtas, bool kWarp>
+template <int V, int K, int kThreads, int kMinCtas, int kSync>
 static cudaError_t launch_slice_tb_v(const PlainArgs &p, const SliceTables &tab, uint32_t n_steps,
                                      cudaStream_t s)
 {
+    constexpr bool kWarp = kSync == kTbWarp;
     constexpr uint32_t TT = uint32_t(kWarp ? 32 : kThreads) * V - 2u * K;
     constexpr uint32_t kPerCta = kWarp ? kThreads / 32 : 1;  // tiles per CTA
     if (n_steps == 0u || n_steps > uint32_t(K)) return cudaErrorInvalidValue;
     const uint32_t Pn = (p.one_L + 7u) & ~7u;
     const uint32_t tiles = (Pn + TT - 1u) / TT;
-    k_step_slice_tb<V, K, kThreads, kMinCtas, kWarp>
+    k_step_slice_tb<V, K, kThreads, kMinCtas, kSync>
         <<<(tiles + kPerCta - 1u) / kPerCta, kThreads, 0, s>>>(p, tab, n_steps);
     return cudaGetLastError();
 }
 
 // Temporally blocked configurations: (nodes per thread, steps per launch,
 // threads per CTA, minimum CTAs per SM, windows per warp or per CTA).
-static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 4, 8, 16, 8};
+static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 4, 8, 16, 16};
 
 uint32_t slice_tb_steps(uint32_t config) { return kTbSteps[config < kSliceTbConfigs ? config : 0]; }
 
@@ -478,12 +520,12 @@ cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t
                             uint32_t config, cudaStream_t s)
 {
     switch (config) {
-    case 0: return launch_slice_tb_v<4, 16, 256, 4, false>(p, tab, n_steps, s);
-    case 1: return launch_slice_tb_v<4, 16, 128, 8, false>(p, tab, n_steps, s);
-    case 2: return launch_slice_tb_v<4, 4, 256, 4, true>(p, tab, n_steps, s);
-    case 3: return launch_slice_tb_v<4, 8, 256, 4, true>(p, tab, n_steps, s);
-    case 4: return launch_slice_tb_v<4, 16, 128, 6, false>(p, tab, n_steps, s);
-    default: return launch_slice_tb_v<4, 8, 128, 8, false>(p, tab, n_steps, s);
+    case 0: return launch_slice_tb_v<4, 16, 256, 4, kTbNeighbours>(p, tab, n_steps, s);
+    case 1: return launch_slice_tb_v<4, 16, 128, 8, kTbBarrier>(p, tab, n_steps, s);
+    case 2: return launch_slice_tb_v<4, 4, 256, 4, kTbWarp>(p, tab, n_steps, s);
+    case 3: return launch_slice_tb_v<4, 8, 256, 4, kTbWarp>(p, tab, n_steps, s);
+    case 4: return launch_slice_tb_v<4, 16, 128, 6, kTbBarrier>(p, tab, n_steps, s);
+    default: return launch_slice_tb_v<4, 16, 256, 3, kTbNeighbours>(p, tab, n_steps, s);
     }
 }
 
