@@ -51,13 +51,17 @@ def test_default_sampler_per_workload():
 
 
 def test_committed_profile_figures():
-    traffic = bench.committed_figure("k_step_slice", "single")
-    assert traffic is not None and 1e8 < traffic < 4e8   # bytes per launch of a 2^24-node step
+    # the blocked kernel moves the state through HBM once per 16-step launch
+    traffic = bench.committed_figure("k_step_slice_tb", "single")
+    assert traffic is not None and 1e8 < traffic < 4e8   # bytes per launch of 16 2^24-node steps
     for key in ("alu_pipe_pct", "issue_active_pct"):
-        v = bench.committed_figure("k_step_slice", "single", key)
+        v = bench.committed_figure("k_step_slice_tb", "single", key)
         assert v is not None and 0 < v <= 100
+    # a summary whose kernel changed after its counters were taken reports null
+    assert bench.committed_figure("k_step_slice", "single") is None
     assert bench.committed_figure("k_step_slice", "no_such_workload") is None
     assert bench.committed_figure("k_step_persistent", "batched") is not None
+    assert bench.committed_figure("k_step_plain", "single", "alu_pipe_pct") is not None
 
 
 @pytest.mark.parametrize("name", ["single", "batched", "uneven"])
