@@ -378,7 +378,8 @@ def config_dict(wl, args, world):
             "C": wl.C, "seed": wl.seed,
             "parallelism": (f"independent lattices x{world}" if single
                             else f"replica batch split over {world} rank(s)"),
-            "l2": ("state (12 B/node double-buffered) larger than L2; no flush"
+            "l2": ("state (12 B/node double-buffered) larger than L2: every launch reads one "
+                   "buffer and writes the other, so no flush"
                    if per_gpu * 12 > 129e6 else "state L2-resident")}
 
 
