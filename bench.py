@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "uneven", "small", "fluct"])
+                    choices=["single", "batched", "uneven", "small", "fluct", "d2q9"])
     ap.add_argument("--u", type=float, default=0.2, help="velocity of the fluct workload")
     ap.add_argument("--C", type=int, default=10,
                     help="sub-collisions per node and step (the paper's runs: 10)")
@@ -701,9 +701,143 @@ def run_gb300(args):
         torch.distributed.destroy_process_group()
 
 
+# D2Q9 workload (Sec. II.B, III.B): one 4096 x 4096 periodic lattice at rho = 36, u = 0, with
+# Poisson(f^eq) occupations, C = 10 and the paper's rates; 9 x uint16 read and written per node-step
+D2Q9_SIDE = 4096
+D2Q9_RHO = 36.0
+D2Q9_BYTES_PER_NODE_STEP = 36
+
+
+def d2q9_metric() -> str:
+    return "D2Q9 site updates per second (10^9, C = 10 particle-pick sub-collisions per node)"
+
+
+def d2q9_oracle_rate(seconds: float, threads: int = 0) -> tuple:
+    """The oracle's D2Q9 steps on a square lattice sized for about `seconds` of host
+    time; returns (GSUPS, nodes, steps, elapsed, threads)."""
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    used = oracle.threads()
+    side = 128
+    while True:
+        S = side * side
+        n0, err = oracle.d2q9_init(side, side, 1, 1, np.full(S, D2Q9_RHO), np.zeros(S), np.zeros(S))
+        t0 = time.perf_counter()
+        n, err = oracle.d2q9_step(side, side, 1, 1, n0, 0, 2)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 8 or side >= 2048:
+            break
+        side *= 2
+    steps = max(2, int(2 * seconds / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    n, err = oracle.d2q9_step(side, side, 1, 1, n0, 0, steps)
+    dt = time.perf_counter() - t0
+    return side * side * steps / dt / 1e9, side * side, steps, dt, used
+
+
+def run_d2q9(args, reference: bool = False):
+    """The D2Q9 line: the GPU kernel (or, with reference, the CPU oracle) on the
+    4096^2 lattice; the same JSON keys as the D1Q3 line."""
+    if reference:
+        gs, nodes, steps, dt, used = d2q9_oracle_rate(args.cpu_seconds)
+        print(json.dumps({"impl": "reference", "metric": d2q9_metric(), "value": gs, "unit": "GSUPS",
+                          "n_gpus": 0, "steps": steps, "warmup": 0,
+                          "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+                          "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+                          "config": {"workload": f"d2q9: {int(nodes ** 0.5)}^2 sample of the "
+                                                 f"{D2Q9_SIDE}^2 lattice, rho = {D2Q9_RHO}, u = 0"},
+                          "cpu_baseline": {"value": gs, "unit": "GSUPS", "cores": used,
+                                           "kind": "oracle",
+                                           "sample": f"{steps} steps of a {nodes}-node square lattice"},
+                          "e2e": {"value": gs, "unit": "GSUPS", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1706_01094_gb300 import build, mclg
+    build.build()
+    side, S = D2Q9_SIDE, D2Q9_SIDE * D2Q9_SIDE
+    stream = torch.cuda.Stream()
+    lat = mclg.Lattice2D(side, side, 1, seed=1 + rank, C=10, lam=mclg.D2Q9_PAPER_LAMBDA,
+                         stream=stream)
+    lat.init(np.full(S, D2Q9_RHO), np.zeros(S), np.zeros(S))
+    tot0 = lat.moments()
+    lat.step(args.warmup)
+    lat.sync()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = NvmlClocks(local)
+    if not clocks.ok:
+        clocks = ClockSampler(local)
+    with clocks:
+        ev0.record(stream)
+        lat.step(args.steps)  # one kernel per step
+        ev1.record(stream)
+        ev1.synchronize()
+    lat.sync()
+    ms = ev0.elapsed_time(ev1)
+    tot1 = lat.moments()
+    assert np.array_equal(tot0, tot1), "mass/momentum not conserved"
+    value = S * args.steps / (ms / 1e3) / 1e9
+    # end to end through the C ABI with pinned host buffers
+    host_in = torch.empty((9, S), dtype=torch.int16).pin_memory()
+    host_out = torch.empty((9, S), dtype=torch.int16).pin_memory()
+    st, tcur = lat.get_state()
+    host_in.copy_(torch.from_numpy(st.view(np.int16)))
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        lat.set_state(host_in, t=tcur + k)
+        lat.step(1)
+        lat.get_state(host_out)
+    e2e = S * e2e_steps / (time.perf_counter() - t0) / 1e9
+    lat.close()
+    if rank != 0:
+        return
+    pk = peaks()
+    hbm_gbs = D2Q9_BYTES_PER_NODE_STEP * S * args.steps / (ms / 1e3) / 1e9
+    alu_pct = committed_figure("k_step_d2q9", "d2q9", "alu_pipe_pct")
+    line = {"metric": d2q9_metric(), "value": value, "unit": "GSUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic: Poisson(f^eq) initial state, rho = 36, u = 0",
+            "config": {"workload": f"d2q9: {side} x {side} periodic lattice, rho = {D2Q9_RHO}, "
+                                   "u = 0, C = 10, the paper's rates (Sec. IV.B)",
+                       "l2": "state (36 B/node double-buffered, 1.2 GB) larger than L2; no flush",
+                       "sms": sm_count(local)},
+            "roofline": {"bound": "alu", "achieved": alu_pct, "peak": 100.0,
+                         "unit": "% of ALU-pipe issue (ncu sm__inst_executed_pipe_alu)",
+                         "frac": None if alu_pct is None else alu_pct / 100.0,
+                         "kernel": "k_step_d2q9",
+                         "issue_active_pct_ncu": committed_figure("k_step_d2q9", "d2q9",
+                                                                  "issue_active_pct"),
+                         "traffic": committed_figure("k_step_d2q9", "d2q9"),
+                         "hbm_equivalent": {"achieved": hbm_gbs, "peak": pk.get("hbm_gbs", 6800.0),
+                                            "unit": "GB/s",
+                                            "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0),
+                                            "bytes_per_node_step": D2Q9_BYTES_PER_NODE_STEP}},
+            "e2e": {"value": e2e, "unit": "GSUPS", "h2d_bytes_per_step": 18 * S,
+                    "d2h_bytes_per_step": 18 * S, "steps": e2e_steps,
+                    "path": "mclg2d_set_state(pinned host) + mclg2d_step(1) + "
+                            "mclg2d_get_state(pinned host)"},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        gs, nodes, steps, dt, used = d2q9_oracle_rate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": gs, "unit": "GSUPS", "cores": used, "kind": "oracle",
+                                "sample": f"{steps} steps of a {nodes}-node square lattice, "
+                                          f"{dt:.1f} s on {used} thread(s)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "d2q9":
+        run_d2q9(args, reference=args.impl == "reference")
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gb300(args)

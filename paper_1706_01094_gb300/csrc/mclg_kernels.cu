@@ -480,15 +480,18 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
     const uint32_t xm = blockIdx.x * kMergePositions + threadIdx.x;
     if (threadIdx.x < kMergePositions && xm < L && n > 0u) {
         const long long *acc = sb[threadIdx.x];
-        const float Rb = float(n);  // samples per position in this batch
-        const float Ma = float(*st.count);  // samples per position before this batch
-        const float Mt = Ma + Rb;
+        // the merge weights from the exact integer counts, rounded to FP32 once
+        // (so they stay exact to FP32 rounding beyond 2^24 samples per position)
+        const uint64_t na = *st.count;  // samples per position before this batch
+        const float Rb = float(n);      // samples per position in this batch (divisor of exact sums)
+        const float wb = float(double(n) / double(na + n));                 // Rb / Mt
+        const float wab = float(double(na) * double(n) / double(na + n));   // Ma Rb / Mt
         float delta[3];
         for (int i = 0; i < 3; ++i) {
             const float mb = float(acc[i]) / Rb;
             const float m = st.mean32[3u * xm + i];
             delta[i] = mb - m;
-            const float inc = delta[i] * (Rb / Mt) - st.mean32c[3u * xm + i];
+            const float inc = delta[i] * wb - st.mean32c[3u * xm + i];
             const float nm = m + inc;
             st.mean32c[3u * xm + i] = (nm - m) - inc;
             st.mean32[3u * xm + i] = nm;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(256) k_stats_merge(unsigned long long *__restr
             // batch co-moment sum (n_i - mb_i)(n_j - mb_j) = (n s_ij - s_i s_j) / n, exact numerator
             const __int128 num = (__int128)n * acc[3 + k] - (__int128)acc[i] * acc[j];
             const float cb = float(num) / Rb;
-            const float inc = cb + delta[i] * delta[j] * (Ma * Rb / Mt) - st.m2c[6u * xm + k];
+            const float inc = cb + delta[i] * delta[j] * wab - st.m2c[6u * xm + k];
             const float m2 = st.m2[6u * xm + k];
             const float nm2 = m2 + inc;
             st.m2c[6u * xm + k] = (nm2 - m2) - inc;
