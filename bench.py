@@ -393,38 +393,36 @@ def graph_launches(steps: int, per_step: int) -> int:
     return steps * per_step + groups + (1 if groups else 0)
 
 
-def stats_merges(steps: int) -> int:
-    """Merge passes of the statistics: one per 32-step graph, one for the rest."""
-    return steps // GRAPH_STEPS + (1 if steps % GRAPH_STEPS else 0)
-
-
 # steps per launch of the slice sampler's temporally blocked variants (14 .. 19);
 # every other variant takes one step per launch
 SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 4, 17: 8, 18: 16, 19: 16}
 
 
 def blocked_span(tuning, wl, stats_on) -> int:
-    if wl.replicas != 1 or stats_on:
+    if stats_on or wl.replicas != 1:
         return 1
     return SLICE_BLOCKED_SPAN.get(int(tuning.get("plain_variant", 0)), 1)
 
 
 def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=False, span=1):
     """Our kernels launched by one mclg_step(steps) call, as the library issues them."""
+    groups = steps // GRAPH_STEPS
+    rest = steps - groups * GRAPH_STEPS
+    if slice_sampler and stats_on:
+        # the statistics form: per step the step kernel and the heavy-node pass;
+        # per 32-step graph a merge and a time advance; per call the threshold
+        # set, the time set (with graphs), the call's last field's partial pass
+        # and the final merge
+        return 2 * steps + 2 * groups + (1 if groups else 0) + 3
     if slice_sampler and span > 1:
         # temporally blocked: one kernel per `span` steps (heavy nodes collided in
         # place); per 32-step graph one time-advance kernel, one time-set per call
-        groups = steps // GRAPH_STEPS
-        rest = steps - groups * GRAPH_STEPS
         return (groups * (GRAPH_STEPS // span) + groups + (1 if groups else 0)
                 + -(-rest // span))
     if slice_sampler:
         # per step: the table kernel and the sequential pass over heavy nodes
-        # (+ statistics: the partial pass every step, the merge pass per batch)
         if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
             return steps * wl.replicas * 2
-        if stats_on:
-            return graph_launches(steps, 3) + stats_merges(steps)
         return graph_launches(steps, 2)
     if persistent:
         long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
@@ -432,8 +430,8 @@ def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=Fa
         return -(-steps // 65536) + (graph_launches(steps, 1) if long_replicas else 0)
     if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
         return steps * wl.replicas  # the per-replica baseline, launched directly
-    if stats_on:  # step, partial pass per step, merge pass per batch
-        return graph_launches(steps, 2) + stats_merges(steps)
+    if stats_on:  # step and partial pass per step, a merge per graph and one per call
+        return graph_launches(steps, 2) + groups + 1
     return graph_launches(steps, 1)
 
 

@@ -19,8 +19,11 @@ def test_launch_counts_follow_the_library_schedule():
     # kernel per 32-step graph and one time-set kernel per call
     assert bench.count_launches(10000, single, 0, False, False, MODES, True) == 20000 + 312 + 1
     assert bench.count_launches(31, single, 0, False, False, MODES, True) == 62   # no graph
-    assert bench.count_launches(64, single, 0, False, True, MODES, True) == 64 * 3 + 2 + 1 + 2
-    assert bench.count_launches(70, single, 0, False, True, MODES, True) == 70 * 3 + 2 + 1 + 3
+    # statistics form: step kernel + heavy pass per step, a merge and a time
+    # advance per graph, threshold set + time set + last partial + final merge
+    assert bench.count_launches(64, single, 0, False, True, MODES, True) == 64 * 2 + 4 + 1 + 3
+    assert bench.count_launches(70, single, 0, False, True, MODES, True) == 70 * 2 + 4 + 1 + 3
+    assert bench.blocked_span({"stats_config": 2, "plain_variant": 14}, single, True) == 1
     # per-replica launches of the baseline mode
     assert bench.count_launches(3, batched, MODES.MODE_PLAIN, False, False, MODES, True) \
         == 3 * batched.replicas * 2
@@ -33,7 +36,6 @@ def test_launch_counts_follow_the_library_schedule():
     assert bench.blocked_span({"plain_variant": 16}, single, False) == 4
     assert bench.blocked_span({"plain_variant": 17}, single, False) == 8
     assert bench.blocked_span({"plain_variant": 4}, single, False) == 1
-    assert bench.blocked_span({"plain_variant": 14}, single, True) == 1     # statistics form
     assert bench.blocked_span({"plain_variant": 14}, batched, False) == 1   # several replicas
     assert bench.count_launches(10000, single, 0, False, False, MODES, True, 16) \
         == 312 * 2 + 312 + 1 + 1
