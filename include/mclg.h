@@ -141,7 +141,9 @@ typedef struct {
                                 draws the current one, 14-19 a temporally blocked form that
                                 advances a window of nodes several steps per launch in
                                 registers; 6-19 apply to single-replica launches; reported by
-                                mclg_tuning).
+                                mclg_tuning).  With MCLG_STATS and the SLICE sampler, v + 1
+                                = use the statistics form's configuration v (0 <= v < 4,
+                                cfg[5] of mclg_tuning).
                                 Every variant gives the same bits; this only fixes the launch
                                 shape. */
     uint32_t node_offset;    /* MCLG_HALO: index of the block's first node in the whole lattice

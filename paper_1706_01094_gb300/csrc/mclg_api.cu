@@ -806,8 +806,9 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     if (S >= (uint64_t(1) << 40)) return MCLG_ERR_ARG;
     if (uint64_t(prm.first_replica) + replicas > (uint64_t(1) << 32)) return MCLG_ERR_ARG;
     if (prm.sampler > MCLG_SAMPLER_SLICE) return MCLG_ERR_ARG;
-    if (prm.kernel_variant >
-        (prm.sampler == MCLG_SAMPLER_SLICE ? kSliceVariants : kPlainVariants))
+    const bool stats_form = (prm.flags & MCLG_STATS) && prm.sampler == MCLG_SAMPLER_SLICE;
+    if (prm.kernel_variant > (stats_form ? kStatsConfigs
+                              : prm.sampler == MCLG_SAMPLER_SLICE ? kSliceVariants : kPlainVariants))
         return MCLG_ERR_ARG;
     if (prm.sampler == MCLG_SAMPLER_SLICE &&
         (prm.C > uint32_t(kSliceMaxC) || prm.slice_n_max > kSliceMaxN))
@@ -820,7 +821,8 @@ mclg_status mclg_create(const uint32_t *L, uint32_t replicas, uint64_t seed, con
     if (!h) return MCLG_ERR_NOMEM;
     h->prm = prm;
     if (prm.kernel_variant) {  // a fixed launch variant: no autotuning
-        h->plain_variant = prm.kernel_variant - 1u;
+        if (stats_form) h->stats_config = prm.kernel_variant - 1u;
+        else h->plain_variant = prm.kernel_variant - 1u;
         h->plain_tuned = true;
     }
     h->seed = seed;

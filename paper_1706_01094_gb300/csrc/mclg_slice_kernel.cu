@@ -777,7 +777,7 @@ __device__ __forceinline__ void node_quantities(uint32_t a, uint32_t b, uint32_t
 }
 
 template <int KR, bool kRed, bool kStream>
-__global__ void __launch_bounds__(256) k_step_slice_stats(PlainArgs p, SliceTables tab, StatsArgs sa)
+__global__ void __launch_bounds__(256, 4) k_step_slice_stats(PlainArgs p, SliceTables tab, StatsArgs sa)
 {
     static_assert(KR >= 1 && KR <= 16, "32-bit counters hold at most 16 products below 2^28");
     constexpr int V = 2;

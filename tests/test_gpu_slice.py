@@ -169,11 +169,13 @@ def test_single_replica_forms_walk_many_tiles(variant):
     assert bad.size == 0, f"{bad.size} nodes differ, first {bad[:5].tolist()}"
 
 
+@pytest.mark.parametrize("config", [None, 0, 3])
 @pytest.mark.parametrize("Lc,R,flags,dense", [(100, 37, 0, False), (33, 5, 0, False),
                                               (1, 3, 0, False), (70, 9, mclg.NO_STREAM, False),
                                               (64, 33, 0, False), (40, 11, 0, True)])
-def test_slice_statistics_form_exact_sums(Lc, R, flags, dense):
-    """The slice step's statistics form (the step kernel adds the field it reads):
+def test_slice_statistics_form_exact_sums(Lc, R, flags, dense, config):
+    """The slice step's statistics form (the step kernel adds the field it reads),
+    autotuned and pinned to two of its configurations (kernel_variant):
     every field after a reset counted once over calls of 5, 33 and 1 steps (graph
     replays among them) and across a reset; tiles with empty positions, ragged
     replica counts, collide-only runs, and values of 2^14 or more (64-bit path)."""
@@ -185,7 +187,10 @@ def test_slice_statistics_form_exact_sums(Lc, R, flags, dense):
     oflags = oracle.FLAG_NO_STREAM if flags & mclg.NO_STREAM else 0
     ref = oracle.Stats(Lc, R)
     n, t = n0, 0
-    with mclg.Lattice(L, seed=6, flags=mclg.STATS | flags, sampler=SLICE) as lat:
+    with mclg.Lattice(L, seed=6, flags=mclg.STATS | flags, sampler=SLICE,
+                      kernel_variant=config) as lat:
+        if config is not None:
+            assert lat.tuning()["stats_config"] == config
         lat.set_state(n0, t=0)
         lat.stats_reset()
         for steps in (5, 33, 1, "reset", 4):
