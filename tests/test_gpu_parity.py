@@ -448,3 +448,28 @@ def test_statistics_merged_at_the_end_of_every_call():
             var32 = st["cov32"][:, [0, 3, 5]].astype(np.float64)
             var64 = st["cov64"][:, [0, 3, 5]]
             assert (np.abs(var32 - var64) / np.abs(var64)).max() <= 1e-6
+
+
+@pytest.mark.parametrize("flags", [0, mclg.NO_STREAM])
+def test_state_transfer_through_pinned_host_buffers(flags):
+    """mclg_set_state / mclg_get_state with pinned host buffers (the e2e path of
+    the benchmark) give the fields of pageable buffers, on ragged replicas, with
+    and without streaming, and agree with the oracle."""
+    L = [1000, 37, 4099, 8]
+    S = sum(L)
+    n0 = workloads.random_state(L, 30.0, seed=9)
+    with mclg.Lattice(L, seed=3, flags=flags) as lat:
+        pin_in = torch.from_numpy(n0.view(np.int16)).pin_memory()
+        lat.set_state(pin_in, t=5)
+        got, t = lat.get_state()                  # pageable, staged
+        assert t == 5 and np.array_equal(got, n0)
+        lat.step(3)
+        want, _ = lat.get_state()
+        pin_out = torch.zeros((3, S), dtype=torch.int16).pin_memory()
+        lat.get_state(pin_out)                     # pinned
+        assert np.array_equal(pin_out.numpy().view(np.uint16), want)
+        lat.set_state(pin_out, t=8)                # and back
+        again, _ = lat.get_state()
+        assert np.array_equal(again, want)
+    ref, err = oracle.step(L, 3, n0, 5, 3, flags=oracle.FLAG_NO_STREAM if flags else 0)
+    assert err == 0 and np.array_equal(want, ref)
