@@ -73,11 +73,12 @@ def parse():
     ap.add_argument("--sampler", default="auto", choices=["auto", "slice", "sequential"],
                     help="slice: the C sub-collisions of a node drawn at once from exact "
                          "cumulative-law tables; sequential: one sub-collision at a time "
-                         "(the persistent batched kernel); auto: slice for the single-lattice "
-                         "and statistics workloads, sequential for the batches")
+                         "(the persistent batched kernel); auto: slice for the single-lattice, "
+                         "statistics and 4096-replica workloads, sequential for the uneven batch")
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
     ap.add_argument("--slice-n-max", type=int, default=0,
-                    help="slice sampler: largest node mass the tables cover (0: the library's 256)")
+                    help="slice sampler: largest node mass the tables cover (0: the library's "
+                         "256; 512 for the 4096-replica workload, whose densities reach 500)")
     ap.add_argument("--kernel-variant", type=int, default=None,
                     help="fix the per-step kernel's launch variant (default: autotuned)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -113,7 +114,7 @@ def committed_figure(kernel: str, workload: str, key: str = "dram_bytes_per_laun
 def pick_sampler(args) -> str:
     if args.sampler != "auto":
         return args.sampler
-    return "slice" if args.workload in ("single", "fluct") else "sequential"
+    return "slice" if args.workload in ("single", "fluct", "batched") else "sequential"
 
 
 class NvmlClocks:
@@ -475,28 +476,36 @@ def timed_steps(lat, stream, steps: int) -> float:
     return e0.elapsed_time(e1)
 
 
+BATCHED_SLICE_N_MAX = 512  # the batch's densities reach 500: tables to mass 512 cover nearly all nodes
+
+
 def batched_extra(mclg, persistent_steps: int = 2000, plain_steps: int = 10) -> dict:
-    """The 4096 x 1024 batch (rho ~ U[5, 500], u ~ U[-0.3, 0.3]): one persistent
-    launch for all its steps against one plain-kernel launch per replica and step
-    (the per-replica baseline, timed on fewer steps: it is launch-bound)."""
+    """The 4096 x 1024 batch (rho ~ U[5, 500], u ~ U[-0.3, 0.3]) with the slice
+    sampler (tables to mass 512): one persistent launch for all its steps against
+    per-replica launches of the per-step kernel (the baseline, timed on fewer
+    steps: it is launch-bound), and the per-step kernel over the whole batch
+    (one launch per step, graph replays) beside them."""
     import torch
     wl = workloads.batched()
     out = {"workload": f"batched: {wl.replicas} replicas x {int(wl.L[0])} nodes, C={wl.C}, "
-                       "rho ~ U[5,500], u ~ U[-0.3,0.3]", "sampler": "sequential"}
+                       "rho ~ U[5,500], u ~ U[-0.3,0.3]", "sampler": "slice",
+           "slice_n_max": BATCHED_SLICE_N_MAX}
     stream = torch.cuda.Stream()
     for name, mode, steps in (("persistent", mclg.MODE_PERSISTENT, persistent_steps),
-                              ("per_replica_plain", mclg.MODE_PLAIN, plain_steps)):
-        with mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode,
-                          stream=stream) as lat:
+                              ("per_replica_plain", mclg.MODE_PLAIN, plain_steps),
+                              ("batched_per_step", mclg.MODE_BATCHED, persistent_steps)):
+        with mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
+                          sampler=mclg.SAMPLER_SLICE, slice_n_max=BATCHED_SLICE_N_MAX) as lat:
             lat.init(wl.rho, wl.u)
             tot0 = lat.totals()
-            lat.step(2)  # autotuning and warm-up
+            lat.step(2)  # tables, autotuning and warm-up
             ms = timed_steps(lat, stream, steps)
             assert np.array_equal(lat.totals(), tot0), "mass/momentum not conserved"
             out[name] = {"gsups": wl.nodes * steps / (ms / 1e3) / 1e9, "steps": steps,
                          "ms_per_step": ms / steps,
                          "launches_per_step": (1.0 / steps if mode == mclg.MODE_PERSISTENT
-                                               else wl.replicas)}
+                                               else 2 * wl.replicas if mode == mclg.MODE_PLAIN
+                                               else 2.0)}
             if mode == mclg.MODE_PERSISTENT:
                 out["tuning"] = lat.tuning()
     out["speedup"] = out["persistent"]["gsups"] / out["per_replica_plain"]["gsups"]
@@ -548,7 +557,8 @@ def run_gb300(args):
     lat = mclg.Lattice(wl.L, seed=wl.seed, C=wl.C, lam=wl.lam, mode=mode, stream=stream,
                        first_replica=first, flags=mclg.STATS if stats_on else 0,
                        sampler=sampler, kernel_variant=args.kernel_variant,
-                       slice_n_max=args.slice_n_max)
+                       slice_n_max=args.slice_n_max or (
+                           BATCHED_SLICE_N_MAX if wl_full.name == "batched" else 0))
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 

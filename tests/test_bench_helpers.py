@@ -44,7 +44,7 @@ def test_launch_counts_follow_the_library_schedule():
 
 
 def test_default_sampler_per_workload():
-    for name, want in (("single", "slice"), ("fluct", "slice"), ("batched", "sequential"),
+    for name, want in (("single", "slice"), ("fluct", "slice"), ("batched", "slice"),
                        ("uneven", "sequential"), ("small", "sequential")):
         args = types.SimpleNamespace(sampler="auto", workload=name)
         assert bench.pick_sampler(args) == want

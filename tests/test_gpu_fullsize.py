@@ -139,3 +139,24 @@ def test_statistics_fp32_bound_beyond_2_to_24_samples():
     assert st["count"] == steps * R > 2**24
     ev, ec = _stats_errors(st)
     assert ev <= 1e-6 and ec <= 1e-6, (ev, ec)
+
+
+def test_batch_whole_field_slice_sampler():
+    """The 4096 x 1024 batch's first 512 replicas (densities across the batch's
+    whole range) with the slice sampler and tables to mass 512, the configuration
+    bench.py times: every node after 20 steps in the persistent kernel (the
+    per-step kernel over a batch is checked bit for bit in test_gpu_slice)."""
+    full = workloads.batched()
+    R = 512
+    L = full.L[:R]
+    rho, u = full.rho[: R * int(L[0])], full.u[: R * int(L[0])]
+    n0, err = oracle.init(L, full.seed, rho, u)
+    assert err == 0
+    want, err = oracle.slice_step(L, full.seed, n0, 0, 20, C=full.C, lam=full.lam, n_max=512)
+    assert err == 0
+    with mclg.Lattice(L, seed=full.seed, mode=mclg.MODE_PERSISTENT, sampler=mclg.SAMPLER_SLICE,
+                      slice_n_max=512) as lat:
+        lat.init(rho, u)
+        lat.step(20)
+        got, _ = lat.get_state()
+    assert np.array_equal(got, want), _diff(got, want)
