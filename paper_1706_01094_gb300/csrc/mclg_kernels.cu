@@ -201,15 +201,15 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, kMinBlocks) k_step_pers
                 uint32_t ln, ld;
                 bool seq0 = true, seq1 = true;
                 if (kSlice) {
-                    // x is even: the pair's top bits are the two halves of one
-                    // word of its eight-node group's block
-                    uint32_t w[4];
-                    slice_top_block(x, rid, t, p.rk, w);
-                    const uint32_t word = pick_word(w, (x >> 1) & 3u);
-                    seq0 = slice_node(a0, b0, c0, word & 0xFFFFu, SliceKey{x, rid, t, p.k0, p.k1},
-                                      p.tab, p.C, err);
-                    seq1 = slice_node(a1, b1, c1, word >> 16, SliceKey{x + 1u, rid, t, p.k0, p.k1},
-                                      p.tab, p.C, err);
+                    // the node pair's table draws (x is even: both nodes' top bits are
+                    // the two halves of one word of their eight-node group's block)
+                    uint32_t a2[2] = {a0, a1}, b2[2] = {b0, b1}, c2[2] = {c0, c1};
+                    const uint32_t heavy =
+                        slice_draws<2>(a2, b2, c2, x, rid, t, p.rk, p.k0, p.k1, p.tab, p.C, err);
+                    a0 = a2[0]; b0 = b2[0]; c0 = c2[0];
+                    a1 = a2[1]; b1 = b2[1]; c1 = c2[1];
+                    seq0 = heavy & 1u;
+                    seq1 = (heavy >> 1) & 1u;
                 }
                 if (seq0) {
                     node_rate(p.galilean != 0u, a0, b0, c0, p.lam_n, p.lam_d, ln, ld);
