@@ -73,12 +73,12 @@ def parse():
     ap.add_argument("--sampler", default="auto", choices=["auto", "slice", "sequential"],
                     help="slice: the C sub-collisions of a node drawn at once from exact "
                          "cumulative-law tables; sequential: one sub-collision at a time "
-                         "(the persistent batched kernel); auto: slice for the single-lattice, "
-                         "statistics and 4096-replica workloads, sequential for the uneven batch")
+                         "(the persistent batched kernel); auto: slice (tables to mass 512 for "
+                         "the batches)")
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent", "batched"])
     ap.add_argument("--slice-n-max", type=int, default=0,
                     help="slice sampler: largest node mass the tables cover (0: the library's "
-                         "256; 512 for the 4096-replica workload, whose densities reach 500)")
+                         "256; 512 for the batches, whose densities reach 500 and 1000)")
     ap.add_argument("--kernel-variant", type=int, default=None,
                     help="fix the per-step kernel's launch variant (default: autotuned)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -114,7 +114,7 @@ def committed_figure(kernel: str, workload: str, key: str = "dram_bytes_per_laun
 def pick_sampler(args) -> str:
     if args.sampler != "auto":
         return args.sampler
-    return "slice" if args.workload in ("single", "fluct", "batched") else "sequential"
+    return "slice" if args.workload in ("single", "fluct", "batched", "uneven") else "sequential"
 
 
 class NvmlClocks:
@@ -415,6 +415,12 @@ def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=Fa
         # set, the time set (with graphs), the call's last field's partial pass
         # and the final merge
         return 2 * steps + 2 * groups + (1 if groups else 0) + 3
+    if persistent:
+        long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
+        # one persistent launch per 65536 steps, plus the long replicas' batched per-step
+        # launches (with the slice sampler each followed by its heavy-node pass)
+        return -(-steps // 65536) + (graph_launches(steps, 2 if slice_sampler else 1)
+                                     if long_replicas else 0)
     if slice_sampler and span > 1:
         # temporally blocked: one kernel per `span` steps (heavy nodes collided in
         # place); per 32-step graph one time-advance kernel, one time-set per call
@@ -425,10 +431,6 @@ def count_launches(steps, wl, mode, persistent, stats_on, mclg, slice_sampler=Fa
         if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
             return steps * wl.replicas * 2
         return graph_launches(steps, 2)
-    if persistent:
-        long_replicas = int((((wl.L.astype(np.int64) + 7) // 8) * 8 > 4096).sum())
-        # one persistent launch per 65536 steps, plus the long replicas' batched plain steps
-        return -(-steps // 65536) + (graph_launches(steps, 1) if long_replicas else 0)
     if mode == mclg.MODE_PLAIN and wl.replicas > 1 and not stats_on:
         return steps * wl.replicas  # the per-replica baseline, launched directly
     if stats_on:  # step and partial pass per step, a merge per graph and one per call
@@ -551,6 +553,8 @@ def run_gb300(args):
         wl, first = sharding.local_workload(wl_full, rank, world)
     mode = {"auto": mclg.MODE_AUTO, "plain": mclg.MODE_PLAIN, "persistent": mclg.MODE_PERSISTENT,
             "batched": mclg.MODE_BATCHED}[args.mode]
+    if args.mode == "auto" and wl_full.name == "uneven":
+        mode = mclg.MODE_PERSISTENT  # the uneven batch's configuration: the persistent kernel
     stream = torch.cuda.Stream()
     sampler_name = pick_sampler(args)
     sampler = mclg.SAMPLER_SLICE if sampler_name == "slice" else mclg.SAMPLER_SEQUENTIAL
@@ -558,7 +562,7 @@ def run_gb300(args):
                        first_replica=first, flags=mclg.STATS if stats_on else 0,
                        sampler=sampler, kernel_variant=args.kernel_variant,
                        slice_n_max=args.slice_n_max or (
-                           BATCHED_SLICE_N_MAX if wl_full.name == "batched" else 0))
+                           BATCHED_SLICE_N_MAX if wl_full.name in ("batched", "uneven") else 0))
     lat.init(wl.rho, wl.u)
     tot0 = lat.totals()
 
@@ -580,8 +584,9 @@ def run_gb300(args):
         clocks = ClockSampler(local)
     with clocks:
         ev0.record(stream)
-        persistent = (mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1)) \
-            and not stats_on and sampler != mclg.SAMPLER_SLICE
+        persistent = (mode == mclg.MODE_PERSISTENT or (mode == mclg.MODE_AUTO and wl.replicas > 1
+                                                       and sampler != mclg.SAMPLER_SLICE)) \
+            and not stats_on
         lat.step(args.steps)  # the library loops over the steps (CUDA graphs where it can)
         ev1.record(stream)
         ev1.synchronize()
@@ -647,7 +652,9 @@ def run_gb300(args):
             # temporally blocked kernel moves the state through HBM once per
             # launch of `span` steps, so its DRAM traffic per launch (committed
             # profile) is far below the algorithmic bytes of its steps
-            kernel = "k_step_slice_tb" if span > 1 else "k_step_slice"
+            # (the persistent form's slice path has no committed profile: its figures stay null)
+            kernel = ("k_step_persistent_slice" if persistent else
+                      "k_step_slice_tb" if span > 1 else "k_step_slice")
             roofline = {"bound": "hbm", **hbm, "traffic": committed_figure(kernel, wl.name),
                         "kernel": kernel, "steps_per_launch": span,
                         "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * wl.nodes * span,

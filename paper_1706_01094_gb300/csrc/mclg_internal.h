@@ -135,7 +135,8 @@ void build_slice_tables(uint32_t n_max, uint32_t C, uint32_t lam_n, uint32_t lam
                         std::vector<uint64_t> &secondary);
 uint64_t slice_records(uint32_t n_max);
 constexpr uint32_t kHeavyCap = 1u << 20;         // heavy-node list entries (overflow: scan)
-constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass (usually empty)
+constexpr uint32_t kHeavyBlocks = 76;            // CTAs of the heavy-node pass of one replica (usually empty)
+constexpr uint32_t kHeavyBatchBlocks = 608;      // of a launch over several replicas (many heavy nodes)
 cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, cudaStream_t s);
 // Temporally blocked slice steps of one replica: n_steps <= slice_tb_steps(config)
 // steps in one launch, from p.in to p.out (heavy nodes collided in place).

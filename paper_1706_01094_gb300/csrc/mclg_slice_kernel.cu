@@ -1008,7 +1008,7 @@ cudaError_t launch_slice(const PlainArgs &p, bool one, const SliceTables &tab, c
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (one) k_step_heavy<true><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
-    else k_step_heavy<false><<<kHeavyBlocks, kPlainThreads, 0, s>>>(p, tab);
+    else k_step_heavy<false><<<kHeavyBatchBlocks, kPlainThreads, 0, s>>>(p, tab);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,9 @@ def test_launch_counts_follow_the_library_schedule():
         == 3 * batched.replicas
     # sequential persistent: one launch per call of at most 65536 steps
     assert bench.count_launches(2000, batched, 0, True, False, MODES) == 1
+    assert bench.count_launches(2000, batched, 0, True, False, MODES, True) == 1  # slice sampler
+    uneven = workloads.uneven()
+    assert bench.count_launches(64, uneven, 2, True, False, MODES, True) == 1 + 64 * 2 + 2 + 1
     # temporally blocked slice launches: 16, 8 or 4 steps each, 2, 4 or 8 per graph
     assert bench.blocked_span({"plain_variant": 14}, single, False) == 16
     assert bench.blocked_span({"plain_variant": 16}, single, False) == 4
@@ -45,7 +48,7 @@ def test_launch_counts_follow_the_library_schedule():
 
 def test_default_sampler_per_workload():
     for name, want in (("single", "slice"), ("fluct", "slice"), ("batched", "slice"),
-                       ("uneven", "sequential"), ("small", "sequential")):
+                       ("uneven", "slice"), ("small", "sequential")):
         args = types.SimpleNamespace(sampler="auto", workload=name)
         assert bench.pick_sampler(args) == want
     assert bench.pick_sampler(types.SimpleNamespace(sampler="sequential", workload="single")) \
