@@ -343,28 +343,45 @@ mclg_status autotune_plain(mclg_ctx *h, uint32_t mode, uint32_t k_begin, uint32_
     MCLG_CK(cudaEventCreate(&e0));
     MCLG_CK(cudaEventCreate(&e1));
     if (fused_stats(h)) {
-        // the statistics form's configurations, timed with no sample counted
-        // (no time step reaches the threshold); the buffer written is the one the
-        // next step overwrites anyway
-        MCLG_CK(launch_set_time(h->d_stats_from, 0xFFFFFFFFu, h->stream));
-        float best = 1e30f;
-        for (uint32_t v = 0; v < kStatsConfigs; ++v) {
-            h->stats_config = v;
-            float ms = 1e30f;
-            for (int rep = 0; rep < 4; ++rep) {
-                MCLG_CK(cudaEventRecord(e0, h->stream));
-                MCLG_CK(plain_step_seq(h, h->cur, h->t, 0, h->R, h->stream, nullptr));
-                MCLG_CK(cudaEventRecord(e1, h->stream));
-                MCLG_CK(cudaEventSynchronize(e1));
-                float one = 0;
-                MCLG_CK(cudaEventElapsedTime(&one, e0, e1));
-                if (rep > 0) ms = std::min(ms, one);
+        // the statistics form's configurations, timed on steps that count their
+        // input field (the configurations differ only in how the sums are
+        // gathered) into scratch sums, so the batch's own stay untouched; the
+        // buffer written is the one the next step overwrites anyway
+        const size_t pb = stats_partials_bytes(h->L[0], h->R);
+        unsigned long long *scratch = nullptr;
+        MCLG_CK(cudaMalloc(&scratch, pb + 3 * sizeof(unsigned long long)));
+        MCLG_CK(cudaMemsetAsync(scratch, 0, pb + 3 * sizeof(unsigned long long), h->stream));
+        unsigned long long *const own_partials = h->d_stat_partials, *const own_count = h->st.count;
+        h->d_stat_partials = scratch;
+        h->st.count = scratch + pb / sizeof(unsigned long long);
+        auto probe = [&]() -> mclg_status {
+            MCLG_CK(launch_set_time(h->d_stats_from, 0u, h->stream));
+            float best = 1e30f;
+            for (uint32_t v = 0; v < kStatsConfigs; ++v) {
+                h->stats_config = v;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 8; ++rep) {
+                    MCLG_CK(cudaEventRecord(e0, h->stream));
+                    MCLG_CK(plain_step_seq(h, h->cur, h->t, 0, h->R, h->stream, nullptr));
+                    MCLG_CK(cudaEventRecord(e1, h->stream));
+                    MCLG_CK(cudaEventSynchronize(e1));
+                    float one = 0;
+                    MCLG_CK(cudaEventElapsedTime(&one, e0, e1));
+                    if (rep > 0) ms = std::min(ms, one);
+                }
+                if (ms < best) {
+                    best = ms;
+                    h->plain_variant = v;  // reported by mclg_tuning
+                }
             }
-            if (ms < best) {
-                best = ms;
-                h->plain_variant = v;  // reported by mclg_tuning
-            }
-        }
+            MCLG_CK(cudaStreamSynchronize(h->stream));
+            return MCLG_OK;
+        };
+        const mclg_status st = probe();
+        h->d_stat_partials = own_partials;
+        h->st.count = own_count;
+        cudaFree(scratch);
+        if (st != MCLG_OK) return st;
         h->stats_config = h->plain_variant;
         h->plain_variant = 0;
         cudaEventDestroy(e0);
