@@ -97,17 +97,25 @@ def peaks():
         return {}
 
 
-def committed_figure(kernel: str, workload: str, key: str = "dram_bytes_per_launch"):
+def committed_figure(kernel: str, workload: str, key: str = "dram_bytes_per_launch",
+                     variant=None):
     """A figure (per-launch DRAM bytes by default) of `kernel` from the committed ncu
-    summary of that kernel on that workload, if there is one."""
+    summary of that kernel on that workload, if there is one.  A summary that names
+    the launch variant it captured gives its figures for that variant only: with
+    `variant` set to another one the figure is None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
-        for line in open(path):
-            if line.startswith(key + ":"):
-                v = (line.split(":", 1)[1].split() or ["null"])[0]
-                return None if v == "null" else float(v)
+        lines = open(path).read().splitlines()
     except OSError:
-        pass
+        return None
+    for line in lines:
+        if variant is not None and line.startswith("variant:"):
+            if int(line.split(":", 1)[1].split()[0]) != int(variant):
+                return None
+    for line in lines:
+        if line.startswith(key + ":"):
+            v = (line.split(":", 1)[1].split() or ["null"])[0]
+            return None if v == "null" else float(v)
     return None
 
 
@@ -396,7 +404,7 @@ def graph_launches(steps: int, per_step: int) -> int:
 
 # steps per launch of the slice sampler's temporally blocked variants (14 .. 19);
 # every other variant takes one step per launch
-SLICE_BLOCKED_SPAN = {14: 16, 15: 16, 16: 4, 17: 8, 18: 16, 19: 16}
+SLICE_BLOCKED_SPAN = {14: 16, 15: 8, 16: 4, 17: 8, 18: 16, 19: 16}
 
 
 def blocked_span(tuning, wl, stats_on) -> int:
@@ -655,12 +663,16 @@ def run_gb300(args):
             # (the persistent form's slice path has no committed profile: its figures stay null)
             kernel = ("k_step_persistent_slice" if persistent else
                       "k_step_slice_tb" if span > 1 else "k_step_slice")
-            roofline = {"bound": "hbm", **hbm, "traffic": committed_figure(kernel, wl.name),
-                        "kernel": kernel, "steps_per_launch": span,
+            # (the blocked kernel's summary holds for the launch variant it captured)
+            pv = tuning.get("plain_variant")
+            roofline = {"bound": "hbm", **hbm,
+                        "traffic": committed_figure(kernel, wl.name, variant=pv),
+                        "kernel": kernel, "launch_variant": pv, "steps_per_launch": span,
                         "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * wl.nodes * span,
-                        "alu_pipe_pct_ncu": committed_figure(kernel, wl.name, "alu_pipe_pct"),
+                        "alu_pipe_pct_ncu": committed_figure(kernel, wl.name, "alu_pipe_pct",
+                                                             variant=pv),
                         "issue_active_pct_ncu": committed_figure(kernel, wl.name,
-                                                                 "issue_active_pct"),
+                                                                 "issue_active_pct", variant=pv),
                         "time_basis": ("whole step: temporally blocked launches of "
                                        f"{span} steps, heavy nodes collided in place"
                                        if span > 1 else

@@ -512,7 +512,7 @@ static cudaError_t launch_slice_tb_v(const PlainArgs &p, const SliceTables &tab,
 
 // Temporally blocked configurations: (nodes per thread, steps per launch,
 // threads per CTA, minimum CTAs per SM, windows per warp or per CTA).
-static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 16, 4, 8, 16, 16};
+static const uint32_t kTbSteps[kSliceTbConfigs] = {16, 8, 4, 8, 16, 16};
 
 uint32_t slice_tb_steps(uint32_t config) { return kTbSteps[config < kSliceTbConfigs ? config : 0]; }
 
@@ -521,7 +521,7 @@ cudaError_t launch_slice_tb(const PlainArgs &p, const SliceTables &tab, uint32_t
 {
     switch (config) {
     case 0: return launch_slice_tb_v<4, 16, 256, 4, kTbNeighbours>(p, tab, n_steps, s);
-    case 1: return launch_slice_tb_v<4, 16, 128, 8, kTbBarrier>(p, tab, n_steps, s);
+    case 1: return launch_slice_tb_v<4, 8, 128, 6, kTbBarrier>(p, tab, n_steps, s);
     case 2: return launch_slice_tb_v<4, 4, 256, 4, kTbWarp>(p, tab, n_steps, s);
     case 3: return launch_slice_tb_v<4, 8, 256, 4, kTbWarp>(p, tab, n_steps, s);
     case 4: return launch_slice_tb_v<4, 16, 128, 6, kTbBarrier>(p, tab, n_steps, s);

@@ -37,6 +37,7 @@ def test_launch_counts_follow_the_library_schedule():
     # temporally blocked slice launches: 16, 8 or 4 steps each, 2, 4 or 8 per graph
     assert bench.blocked_span({"plain_variant": 14}, single, False) == 16
     assert bench.blocked_span({"plain_variant": 16}, single, False) == 4
+    assert bench.blocked_span({"plain_variant": 15}, single, False) == 8
     assert bench.blocked_span({"plain_variant": 17}, single, False) == 8
     assert bench.blocked_span({"plain_variant": 4}, single, False) == 1
     assert bench.blocked_span({"plain_variant": 14}, batched, False) == 1   # several replicas
@@ -62,6 +63,10 @@ def test_committed_profile_figures():
     for key in ("alu_pipe_pct", "issue_active_pct"):
         v = bench.committed_figure("k_step_slice_tb", "single", key)
         assert v is not None and 0 < v <= 100
+    # the blocked kernel's summary holds for the variant it captured only
+    assert bench.committed_figure("k_step_slice_tb", "single", variant=18) == traffic
+    assert bench.committed_figure("k_step_slice_tb", "single", variant=15) is None
+    assert bench.committed_figure("k_step_slice_tb", "single", "alu_pipe_pct", variant=15) is None
     # a summary whose kernel changed after its counters were taken reports null
     assert bench.committed_figure("k_step_slice", "single") is None
     assert bench.committed_figure("k_step_slice", "no_such_workload") is None

@@ -249,7 +249,7 @@ def test_slice_persistent_full_size_batch_prefix():
 
 # tiles of the temporally blocked configurations (window E = threads of the CTA,
 # or of the warp, x nodes per thread; halo K on each side)
-_TB_TILES = {14: 992, 15: 480, 16: 120, 17: 112, 18: 480, 19: 992}
+_TB_TILES = {14: 992, 15: 496, 16: 120, 17: 112, 18: 480, 19: 992}
 
 
 @pytest.mark.parametrize("variant", range(14, 20))
