@@ -45,6 +45,10 @@ def test_launch_counts_follow_the_library_schedule():
         == 312 * 2 + 312 + 1 + 1
     assert bench.count_launches(20, single, 0, False, False, MODES, True, 16) == 2
     assert bench.count_launches(64, single, 0, False, False, MODES, True, 8) == 8 + 2 + 1
+    # the counts the GPU run of the 8-step windows reported: 10000 steps in 1563 launches
+    # (1250 blocked launches, 312 time advances, one time set), 20 steps in 3 (8 + 8 + 4)
+    assert bench.count_launches(10000, single, 0, False, False, MODES, True, 8) == 1563
+    assert bench.count_launches(20, single, 0, False, False, MODES, True, 8) == 3
 
 
 def test_default_sampler_per_workload():
